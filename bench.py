@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the multiple-double least-squares path on GB300.
+
+Metric: md QR+backsub TFLOPS (paper op counts) at dd/qd/od -- the md operations
+of the unblocked Householder least-squares method (QR of [A | b], then back
+substitution) converted to double-precision flops with Table 1 of
+arXiv 2110.08375, divided by the device time.
+
+Workload (one "step"): the dense least-squares solve m = n = 1024, tile 128
+(eight tiles), in double double, quad double and octo double, entries of A and
+b ~ U[-1,1) per limb recipe, seed 0.  Inputs are resident in HBM before the
+timed region; L2 (129 MB) is flushed between steps by writing a 256 MiB
+buffer outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank solves its own replica of the workload (the
+single solve does not shard); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "md QR+backsub TFLOPS (paper op counts) at dd/qd/od"
+PREC_NAMES = {2: "dd", 4: "qd", 8: "od"}
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mdls", choices=["mdls", "reference"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--tile", type=int, default=128)
+    ap.add_argument("--precs", default="2,4,8")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "mdls" else "gloo"
+        if args.impl == "mdls":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(self.rows), "reasons": reasons}
+
+
+def workload_flops(precs, n):
+    from paper_2110_08375_gb300 import opcount
+    return {p: opcount.lstsq_table1_flops(p, n, n) for p in precs}
+
+
+def cpu_baseline(n_sample: int, precs, seed: int = 0) -> dict:
+    """The oracle (plain C, OpenMP) on a bounded sample of the workload: the
+    leading n_sample x n_sample block of each precision's A and the leading
+    n_sample entries of b, solved in every precision."""
+    import oracle
+    import synth
+    from paper_2110_08375_gb300 import opcount
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    flops = 0
+    t0 = time.perf_counter()
+    for p in precs:
+        A, b = synth.lstsq_problem(p, 1024, 1024, seed=seed, tag="cfg1")
+        As = A[:, :n_sample, :n_sample].copy()
+        bs = b[:, :n_sample].copy()
+        oracle.lstsq(As, bs)
+        flops += opcount.lstsq_table1_flops(p, n_sample, n_sample)
+    dt = time.perf_counter() - t0
+    return {"value": flops / dt / 1e12, "unit": "TFLOPS", "cores": cores, "kind": "oracle",
+            "sample": f"lstsq of the leading {n_sample}x{n_sample} block of the n=1024 inputs, "
+                      f"precisions {','.join(PREC_NAMES[p] for p in precs)}; {dt:.1f} s",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args)
+    precs = [int(x) for x in args.precs.split(",")]
+    if rank != 0:
+        barrier(world)
+        return
+    n_sample = 192
+    for _ in range(args.warmup):
+        cpu_baseline(n_sample, precs)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = cpu_baseline(n_sample, precs)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    value = statistics.mean(vals)
+    cb = dict(r)
+    cb["value"] = value
+    cb.pop("seconds", None)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"lstsq sample {n_sample}x{n_sample} of m=n={args.n}, dd/qd/od, seed 0",
+                       "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "TFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2110_08375_gb300 as mdls
+    import synth
+    from paper_2110_08375_gb300 import opcount
+
+    rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    precs = [int(x) for x in args.precs.split(",")]
+    n, t = args.n, args.tile
+    stream = torch.cuda.current_stream()
+
+    host = {}
+    data = {}
+    for p in precs:
+        A, b = synth.lstsq_problem(p, n, n, seed=0, tag="cfg1")
+        host[p] = (torch.from_numpy(A).pin_memory(), torch.from_numpy(b).pin_memory())
+        Ad, bd = host[p][0].to(dev), host[p][1].to(dev)
+        xd = torch.zeros((p, n), dtype=torch.float64, device=dev)
+        ws = mdls.workspace(mdls.mdls_lstsq_workspace(p, n, n, t), dev)
+        data[p] = (Ad, bd, xd, ws)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        for p in precs:
+            Ad, bd, xd, ws = data[p]
+            mdls.mdls_lstsq(Ad, bd, xd, tile=t, ws=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for p in precs:
+        st = mdls.mdls_read_status(data[p][3])
+        if st != 0:
+            raise RuntimeError(f"device status {mdls.status_string(st)} for p={p}")
+
+    # timed region: K steps, L2 flushed before each (outside the events)
+    mdls.mdls_profile_enable(True)
+    mdls.mdls_profile_read()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(precs) + 1)] for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        for k, p in enumerate(precs):
+            Ad, bd, xd, ws = data[p]
+            mdls.mdls_lstsq(Ad, bd, xd, tile=t, ws=ws)
+            ev[i][k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    stages = mdls.mdls_profile_read()
+    mdls.mdls_profile_enable(False)
+    per_prec_ms = {p: sum(ev[i][k].elapsed_time(ev[i][k + 1]) for i in range(args.steps))
+                   for k, p in enumerate(precs)}
+    total_ms = sum(ev[i][0].elapsed_time(ev[i][-1]) for i in range(args.steps))
+    total_ms = max_over_ranks(total_ms, world)
+    fl = workload_flops(precs, n)
+    step_flops = sum(fl.values())
+    value = world * step_flops * args.steps / (total_ms / 1e3) / 1e12
+
+    # roofline of the dominant stage (trailing-update md GEMMs, FP64 ALU bound)
+    trail_ms = stages["trailing"][0]
+    trail_flops = sum(opcount.trailing_md_fmas(n, n, t, extra_cols=1) * opcount.fma_cost(p)[1]
+                      for p in precs) * args.steps
+    dominant = max(stages, key=lambda k: stages[k][0])
+    achieved = trail_flops / (trail_ms / 1e3) / 1e12 if trail_ms > 0 else None
+    roofline = {"bound": "alu", "kernel": "gemm_kernel (trailing update C += Y (W^T C))",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                "peak_source": "2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "dominant_stage": dominant}
+
+    out = {"metric": METRIC, "value": value, "unit": "TFLOPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"least squares m=n={n}, tile {t} ({-(-n // t)} tiles), "
+                                  f"{'+'.join(PREC_NAMES[p] for p in precs)}, seed 0",
+                      "l2": "flushed before every timed step (256 MiB write, outside the events)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "clocks": clocks,
+           "gpu_launches": int(sum(v[1] for v in stages.values())),
+           "roofline": roofline,
+           "per_prec": {PREC_NAMES[p]: {"ms": per_prec_ms[p] / args.steps,
+                                        "tflops": fl[p] / (per_prec_ms[p] / args.steps / 1e3) / 1e12}
+                        for p in precs},
+           "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()}}
+
+    # end to end through the public API with host buffers: H2D of A and b, the
+    # solve, D2H of x, every step
+    if not args.no_e2e:
+        xs_host = {p: torch.empty((p, n), dtype=torch.float64).pin_memory() for p in precs}
+        h2d = sum(host[p][0].numel() * 8 + host[p][1].numel() * 8 for p in precs)
+        d2h = sum(xs_host[p].numel() * 8 for p in precs)
+
+        def e2e_step():
+            for p in precs:
+                Ad, bd, xd, ws = data[p]
+                Ad.copy_(host[p][0], non_blocking=True)
+                bd.copy_(host[p][1], non_blocking=True)
+                mdls.mdls_lstsq(Ad, bd, xd, tile=t, ws=ws)
+                xs_host[p].copy_(xd, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2e_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0.record(stream)
+            e2e_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+        e2e_ms = max_over_ranks(e2e_ms, world)
+        out["e2e"] = {"value": world * step_flops * args.steps / (e2e_ms / 1e3) / 1e12, "unit": "TFLOPS",
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "ms_per_step": e2e_ms / args.steps}
+        # the e2e answers match the device-resident answers
+        for p in precs:
+            assert torch.equal(xs_host[p], data[p][2].cpu())
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(128, precs)
+        out["cpu_baseline"].pop("seconds", None)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    barrier(world)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * mdls.h -- multiple-double least squares on one GB300 GPU (sm_103a).
+ *
+ * C ABI of libmdls.so.  The operations follow arXiv 2110.08375 ("Least Squares
+ * on GPUs in Multiple Double Precision", J. Verschelde):
+ *   - the problem (Section 1): the least squares solution x of A x = b
+ *     minimises ||b - A x||_2^2; A = QR reduces it to R x = Q^T b, solved by
+ *     back substitution;
+ *   - multiple-double numbers (Section 1.1): an unevaluated sum of p doubles,
+ *     p = 2 (double double), 4 (quad double), 8 (octo double);
+ *   - blocked Householder QR (Section 3, Algorithm 2) with the WY
+ *     representation P = I + W Y^T of each tile (Section 3, equations for
+ *     P_WY and z = -beta (v + W Y^T v));
+ *   - tiled back substitution with inverted diagonal tiles (Section 2,
+ *     Algorithm 1).
+ *
+ * STORAGE (all matrices and vectors): limb-planar, as in the paper's Section 2
+ * ("an array of m matrices, U_1 holds the most significant doubles").  Limb l
+ * (0 = most significant) of entry (i, j) of a matrix is at
+ *     ptr[l * ps + j * ld + i]            (column-major planes),
+ * with ld >= rows and ps >= ld * cols (plane stride, in doubles).  Limb l of
+ * entry i of a vector is at ptr[l * ps + i].  Inputs are read as the sum of
+ * their limbs and must be normalised (|limb_{k+1}| <= ulp(limb_k)); outputs
+ * are normalised the same way (to within a factor 2).
+ *
+ * POINTERS: every matrix, vector and workspace pointer is a DEVICE pointer
+ * (cudaMalloc'd or equivalent) owned by the caller.  The library allocates
+ * nothing: scratch space is the caller's workspace `ws`, at least as large as
+ * the matching *_workspace() query, 256-byte aligned.  A workspace may be
+ * reused by consecutive calls on the same stream, never by two calls that run
+ * concurrently.
+ *
+ * STREAM: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ * asynchronous: they enqueue kernels and return.  Host-detectable errors are
+ * returned at once (negative codes below) and nothing is enqueued.  Errors
+ * only the device can detect (a zero pivot, a bounded wait that gave up) are
+ * recorded in the workspace status word, readable with mdls_read_status()
+ * after the call.
+ *
+ * PRECISION `prec`: 2, 4 or 8 limbs.  TILE `tile`: tile size t in 1..256 (the
+ * paper's n), 0 = default (128, or the problem size when smaller).  The last
+ * tile may be narrower than t ("ragged"), so n need not be a multiple of t.
+ */
+#ifndef MDLS_H
+#define MDLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MDLS_OK 0
+#define MDLS_ERR_ARG (-1)         /* bad size, stride, pointer or tile   */
+#define MDLS_ERR_PREC (-2)        /* prec not in {2, 4, 8}                */
+#define MDLS_ERR_WORKSPACE (-3)   /* ws too small, NULL or misaligned     */
+#define MDLS_ERR_SINGULAR (-4)    /* device: zero pivot on R's diagonal   */
+#define MDLS_ERR_CUDA (-5)        /* a kernel launch failed               */
+#define MDLS_ERR_TIMEOUT (-6)     /* device: a bounded wait gave up       */
+#define MDLS_ERR_UNSUPPORTED (-7) /* valid request this build cannot run  */
+
+/* arithmetic modes of the QR and least-squares calls */
+#define MDLS_MODE_PLAIN 0 /* all arithmetic in md on the FP64 CUDA cores */
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int mdls_version(void);
+
+/* Human-readable text of a status code (static storage). */
+const char* mdls_status_string(int code);
+
+/*
+ * mdls_qr -- blocked Householder QR, Algorithm 2 of the paper (Section 3).
+ *   A (m x n, m >= n >= 1), in place: on return its upper triangle holds R
+ *     (diagonal >= 0; reflectors follow Golub & Van Loan Alg. 5.1.1 so that
+ *     each P x = ||x|| e1) and its strictly lower part is exactly zero.
+ *   Q (m x m) receives the orthogonal factor with A = Q R when Q != NULL
+ *     (Algorithm 2's output); ldq >= m, psq >= ldq * m.  Q must not overlap A.
+ *   mode: MDLS_MODE_PLAIN.
+ * Per tile of t columns: the Householder vectors of the tile, its WY form
+ * (P = I + W Y^T), then the trailing update C := C + Y (W^T C).  Q is
+ * accumulated backward from the identity, Q := P_k Q for k = N..1.
+ * Workspace: mdls_qr_workspace(prec, m, n, tile, Q != NULL, mode) bytes.
+ * Returns MDLS_OK or a negative status; device-side failures (timeout of a
+ * bounded wait) are recorded in the workspace status.
+ */
+int mdls_qr(int prec, int64_t m, int64_t n, double* A, int64_t lda, int64_t psa, double* Q,
+            int64_t ldq, int64_t psq, int tile, int mode, void* ws, size_t ws_bytes,
+            void* stream);
+size_t mdls_qr_workspace(int prec, int64_t m, int64_t n, int tile, int want_q, int mode);
+
+/*
+ * mdls_backsub -- tiled accelerated back substitution, Algorithm 1 of the
+ * paper (Section 2): solves R x = y for the upper triangular n x n R (only
+ * the upper triangle is read; diagonal nonzero).
+ *   Step 1 inverts the N = ceil(n / t) diagonal tiles (one thread per column
+ *   of each inverse, solving U v = e_k).  Step 2 runs i = N..1:
+ *   x_i := U_i^{-1} y_i, then y_j := y_j - A_{j,i} x_i for all j < i at once.
+ *   R, y are not modified; x (length n, plane stride psx >= n) is written.
+ *   A zero diagonal entry records MDLS_ERR_SINGULAR in the workspace status.
+ * Workspace: mdls_backsub_workspace(prec, n, tile) bytes.
+ */
+int mdls_backsub(int prec, int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y,
+                 int64_t psy, double* x, int64_t psx, int tile, void* ws, size_t ws_bytes,
+                 void* stream);
+size_t mdls_backsub_workspace(int prec, int64_t n, int tile);
+
+/*
+ * mdls_lstsq -- least squares solution of A x = b (Section 1): the blocked QR
+ * of Algorithm 2 applied to [A | b] (so Q^T b is formed by the same WY
+ * updates and Q itself is never built), followed by Algorithm 1 on
+ * R x = (Q^T b)[0:n].  A (m x n, m >= n >= 1) and b (length m) are read
+ * only; x (length n) is written.  The working copy of [A | b] lives in ws.
+ * Workspace: mdls_lstsq_workspace(prec, m, n, tile, mode) bytes.
+ */
+int mdls_lstsq(int prec, int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa,
+               const double* b, int64_t psb, double* x, int64_t psx, int tile, int mode, void* ws,
+               size_t ws_bytes, void* stream);
+size_t mdls_lstsq_workspace(int prec, int64_t m, int64_t n, int tile, int mode);
+
+/*
+ * mdls_vec_op -- elementwise multiple-double arithmetic on device vectors
+ * (Section 1.1: the md add, mul, div of Table 1, and sqrt):
+ *   op MDLS_OP_ADD: c = a + b     MDLS_OP_SUB: c = a - b
+ *      MDLS_OP_MUL: c = a * b     MDLS_OP_DIV: c = a / b
+ *      MDLS_OP_FMA: c = c + a * b MDLS_OP_SQRT: c = sqrt(a) (b unused)
+ * count entries, limb-planar with plane strides psa, psb, psc (>= count).
+ * c may alias a or b.  Division by zero and sqrt of a negative number give
+ * IEEE non-finite limbs; no status is recorded.
+ */
+#define MDLS_OP_ADD 0
+#define MDLS_OP_SUB 1
+#define MDLS_OP_MUL 2
+#define MDLS_OP_DIV 3
+#define MDLS_OP_FMA 4
+#define MDLS_OP_SQRT 5
+int mdls_vec_op(int prec, int op, int64_t count, const double* a, int64_t psa, const double* b,
+                int64_t psb, double* c, int64_t psc, void* stream);
+
+/*
+ * mdls_read_status -- waits for `stream`, then copies the device status word
+ * of the workspace `ws` (MDLS_OK, MDLS_ERR_SINGULAR or MDLS_ERR_TIMEOUT) to
+ * *status.  Returns MDLS_OK or MDLS_ERR_CUDA.
+ */
+int mdls_read_status(const void* ws, int* status, void* stream);
+
+/*
+ * Per-stage timing, as the paper measures its kernels (Section 4.2: every
+ * launch timed with cudaEventElapsedTime, sums reported per stage of
+ * Algorithms 1 and 2).  Launches are always counted per stage.
+ * mdls_profile_enable(1) additionally records a CUDA event pair around every
+ * launch on its stream.  mdls_profile_read() waits for those events, writes
+ * up to `cap` per-stage sums (milliseconds; NULL to skip) and launch counts
+ * (NULL to skip), resets them, and returns the number of stages (or a
+ * negative status).  Stage indices: 0 panel, 1 compute W, 2 trailing update,
+ * 3 Q accumulation, 4 invert diagonal tiles, 5 multiply with inverses,
+ * 6 back substitution updates, 7 other; mdls_stage_name() names them.
+ * The profiler is process-wide; timing is meant for one thread at a time.
+ */
+void mdls_profile_enable(int on);
+int mdls_profile_read(double* ms, int64_t* launches, int cap);
+const char* mdls_stage_name(int stage);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDLS_H */

@@ -1,0 +1,226 @@
+"""Multiple-double least squares on one GB300 (arXiv 2110.08375), CUDA path.
+
+This module is a thin ctypes binding of ``libmdls.so`` (C ABI declared in
+``include/mdls.h``): it marshals torch tensors to device pointers, sizes and
+strides, and raises on error codes.  Every step of the computation runs in the
+library's CUDA kernels; there is no CPU fallback.  If the library is missing
+or no GPU is present, calls fail loudly.
+
+Tensor convention (limb-planar, as in the paper's Section 2): an md matrix
+with ``rows x cols`` entries is a float64 CUDA tensor of shape
+``(p, cols, ld)`` whose planes are column-major (``ld >= rows``); a vector of
+length n is ``(p, n)``.  p = 2 (double double), 4 (quad double), 8 (octo
+double).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmdls.so")
+
+MDLS_OK = 0
+MDLS_ERR_ARG = -1
+MDLS_ERR_PREC = -2
+MDLS_ERR_WORKSPACE = -3
+MDLS_ERR_SINGULAR = -4
+MDLS_ERR_CUDA = -5
+MDLS_ERR_TIMEOUT = -6
+MDLS_ERR_UNSUPPORTED = -7
+MODE_PLAIN = 0
+OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "fma": 4, "sqrt": 5}
+
+_lib = None
+
+
+class MdlsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+def lib() -> C.CDLL:
+    """Loads libmdls.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libmdls.so not built at {LIB_PATH}; run paper_2110_08375_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    i64, vp, sz = C.c_int64, C.c_void_p, C.c_size_t
+    L.mdls_version.restype = C.c_int
+    L.mdls_status_string.restype = C.c_char_p
+    L.mdls_status_string.argtypes = [C.c_int]
+    L.mdls_qr.argtypes = [C.c_int, i64, i64, vp, i64, i64, vp, i64, i64, C.c_int, C.c_int, vp, sz, vp]
+    L.mdls_qr_workspace.argtypes = [C.c_int, i64, i64, C.c_int, C.c_int, C.c_int]
+    L.mdls_qr_workspace.restype = sz
+    L.mdls_backsub.argtypes = [C.c_int, i64, vp, i64, i64, vp, i64, vp, i64, C.c_int, vp, sz, vp]
+    L.mdls_backsub_workspace.argtypes = [C.c_int, i64, C.c_int]
+    L.mdls_backsub_workspace.restype = sz
+    L.mdls_lstsq.argtypes = [C.c_int, i64, i64, vp, i64, i64, vp, i64, vp, i64, C.c_int, C.c_int, vp,
+                             sz, vp]
+    L.mdls_lstsq_workspace.argtypes = [C.c_int, i64, i64, C.c_int, C.c_int]
+    L.mdls_lstsq_workspace.restype = sz
+    L.mdls_read_status.argtypes = [vp, C.POINTER(C.c_int), vp]
+    L.mdls_profile_enable.argtypes = [C.c_int]
+    L.mdls_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
+    L.mdls_stage_name.argtypes = [C.c_int]
+    L.mdls_stage_name.restype = C.c_char_p
+    L.mdls_vec_op.argtypes = [C.c_int, C.c_int, i64, vp, i64, vp, i64, vp, i64, vp]
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return lib().mdls_status_string(int(code)).decode()
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the multiple-double CUDA path needs a CUDA GPU")
+    return torch
+
+
+def _check_md(t, ndim: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if t.dim() != ndim or t.shape[0] not in (2, 4, 8):
+        raise ValueError(f"{name} must have shape (p, ...) with p in (2, 4, 8) and {ndim} dims")
+    if t.stride(-1) != 1:
+        raise ValueError(f"{name}: innermost dimension must be contiguous")
+
+
+def _stream(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def workspace(nbytes: int, device=None):
+    """A 256-byte aligned device buffer of at least nbytes (torch allocation)."""
+    torch = _torch()
+    buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device or "cuda")
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + int(nbytes)]
+
+
+def mdls_qr_workspace(prec: int, m: int, n: int, tile: int = 0, want_q: bool = True,
+                      mode: int = MODE_PLAIN) -> int:
+    return int(lib().mdls_qr_workspace(prec, m, n, tile, int(want_q), mode))
+
+
+def mdls_backsub_workspace(prec: int, n: int, tile: int = 0) -> int:
+    return int(lib().mdls_backsub_workspace(prec, n, tile))
+
+
+def mdls_lstsq_workspace(prec: int, m: int, n: int, tile: int = 0, mode: int = MODE_PLAIN) -> int:
+    return int(lib().mdls_lstsq_workspace(prec, m, n, tile, mode))
+
+
+def mdls_qr(A, Q=None, rows: int | None = None, tile: int = 0, mode: int = MODE_PLAIN, ws=None,
+            stream=None):
+    """In-place blocked Householder QR (Algorithm 2).  A: (p, n, ld); on return
+    its upper triangle is R and the rest zero.  Q: (p, m, ldq) or None."""
+    _check_md(A, 3, "A")
+    p, n, lda = A.shape
+    m = lda if rows is None else int(rows)
+    if Q is not None:
+        _check_md(Q, 3, "Q")
+    need = mdls_qr_workspace(p, m, n, tile, Q is not None, mode)
+    if need == 0:
+        raise MdlsError(MDLS_ERR_ARG, "mdls_qr_workspace")
+    if ws is None:
+        ws = workspace(need, A.device)
+    rc = lib().mdls_qr(p, m, n, A.data_ptr(), A.stride(1), A.stride(0),
+                       Q.data_ptr() if Q is not None else None,
+                       Q.stride(1) if Q is not None else 0, Q.stride(0) if Q is not None else 0,
+                       tile, mode, ws.data_ptr(), ws.numel() * ws.element_size(), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_qr")
+    return ws
+
+
+def mdls_backsub(R, y, x, tile: int = 0, ws=None, stream=None):
+    """Algorithm 1: solves R x = y (R: (p, n, ld) upper triangular; y, x: (p, n))."""
+    _check_md(R, 3, "R"); _check_md(y, 2, "y"); _check_md(x, 2, "x")
+    p, n, ldr = R.shape
+    need = mdls_backsub_workspace(p, n, tile)
+    if need == 0:
+        raise MdlsError(MDLS_ERR_ARG, "mdls_backsub_workspace")
+    if ws is None:
+        ws = workspace(need, R.device)
+    rc = lib().mdls_backsub(p, n, R.data_ptr(), R.stride(1), R.stride(0), y.data_ptr(), y.stride(0),
+                            x.data_ptr(), x.stride(0), tile, ws.data_ptr(),
+                            ws.numel() * ws.element_size(), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_backsub")
+    return ws
+
+
+def mdls_lstsq(A, b, x, rows: int | None = None, tile: int = 0, mode: int = MODE_PLAIN, ws=None,
+               stream=None):
+    """Least squares min ||b - A x|| (A: (p, n, ld), b: (p, m), x: (p, n))."""
+    _check_md(A, 3, "A"); _check_md(b, 2, "b"); _check_md(x, 2, "x")
+    p, n, lda = A.shape
+    m = lda if rows is None else int(rows)
+    need = mdls_lstsq_workspace(p, m, n, tile, mode)
+    if need == 0:
+        raise MdlsError(MDLS_ERR_ARG, "mdls_lstsq_workspace")
+    if ws is None:
+        ws = workspace(need, A.device)
+    rc = lib().mdls_lstsq(p, m, n, A.data_ptr(), A.stride(1), A.stride(0), b.data_ptr(), b.stride(0),
+                          x.data_ptr(), x.stride(0), tile, mode, ws.data_ptr(),
+                          ws.numel() * ws.element_size(), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_lstsq")
+    return ws
+
+
+def mdls_read_status(ws, stream=None) -> int:
+    """Synchronises the stream and returns the device status word of ws."""
+    st = C.c_int(0)
+    rc = lib().mdls_read_status(ws.data_ptr(), C.byref(st), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_read_status")
+    return st.value
+
+
+def mdls_vec_op(op: str, a, b=None, c=None, stream=None):
+    """Elementwise md arithmetic: c = a op b (op in add, sub, mul, div, fma:
+    c = c + a*b, sqrt: c = sqrt(a)).  a, b, c: (p, n) tensors."""
+    torch = _torch()
+    _check_md(a, 2, "a")
+    if c is None:
+        c = torch.zeros_like(a)
+    bb = a if b is None else b
+    rc = lib().mdls_vec_op(a.shape[0], OPS[op], a.shape[1], a.data_ptr(), a.stride(0),
+                           bb.data_ptr(), bb.stride(0), c.data_ptr(), c.stride(0), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_vec_op")
+    return c
+
+
+N_STAGES = 8
+STAGE_KEYS = ("panel", "compute_w", "trailing", "q_accum", "invert_tiles", "mul_inverses",
+              "bs_update", "other")
+
+
+def mdls_profile_enable(on: bool = True) -> None:
+    lib().mdls_profile_enable(int(bool(on)))
+
+
+def mdls_profile_read() -> dict:
+    """Per-stage (milliseconds, launches) since the last read; resets them."""
+    ms = (C.c_double * N_STAGES)()
+    cnt = (C.c_int64 * N_STAGES)()
+    rc = lib().mdls_profile_read(ms, cnt, N_STAGES)
+    if rc < 0:
+        raise MdlsError(rc, "mdls_profile_read")
+    return {k: (ms[i], int(cnt[i])) for i, k in enumerate(STAGE_KEYS)}
+
+
+def mdls_stage_name(stage: int) -> str:
+    return lib().mdls_stage_name(int(stage)).decode()

@@ -1,0 +1,148 @@
+// C ABI of libmdls (declared in include/mdls.h): argument checks, workspace
+// sizes and dispatch to the per-precision instantiations.
+#include <cuda_runtime.h>
+
+#include "../../include/mdls.h"
+#include "layout.h"
+
+namespace mdls {
+#define MDLS_DECLARE(P)                                                                           \
+    int qr_entry_p##P(int64_t, int64_t, double*, int64_t, int64_t, double*, int64_t, int64_t, int, \
+                      void*, cudaStream_t);                                                        \
+    int bs_entry_p##P(int64_t, const double*, int64_t, int64_t, const double*, int64_t, double*,  \
+                      int64_t, int, void*, cudaStream_t);                                          \
+    int ls_entry_p##P(int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t,  \
+                      double*, int64_t, int, void*, cudaStream_t);                                 \
+    int vec_entry_p##P(int, int64_t, const double*, int64_t, const double*, int64_t, double*,     \
+                       int64_t, cudaStream_t);
+MDLS_DECLARE(2)
+MDLS_DECLARE(4)
+MDLS_DECLARE(8)
+}  // namespace mdls
+
+using namespace mdls;
+
+static bool prec_ok(int p) { return p == 2 || p == 4 || p == 8; }
+
+static bool ws_ok(const void* ws, size_t have, size_t need) {
+    return ws != nullptr && have >= need && (reinterpret_cast<uintptr_t>(ws) & 255) == 0;
+}
+
+extern "C" {
+
+int mdls_version(void) { return 100; }
+
+const char* mdls_status_string(int code) {
+    switch (code) {
+        case MDLS_OK: return "ok";
+        case MDLS_ERR_ARG: return "invalid argument (size, stride, pointer or tile)";
+        case MDLS_ERR_PREC: return "precision must be 2, 4 or 8 limbs";
+        case MDLS_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+        case MDLS_ERR_SINGULAR: return "zero pivot on the diagonal of R";
+        case MDLS_ERR_CUDA: return "CUDA launch or copy failed";
+        case MDLS_ERR_TIMEOUT: return "a bounded device wait gave up";
+        case MDLS_ERR_UNSUPPORTED: return "request not supported by this build or device";
+        default: return "unknown status";
+    }
+}
+
+size_t mdls_qr_workspace(int prec, int64_t m, int64_t n, int tile, int want_q, int mode) {
+    int t = norm_tile(tile, n);
+    if (!prec_ok(prec) || t < 1 || m < n || n < 1 || mode != MDLS_MODE_PLAIN) return 0;
+    size_t total = 0;
+    qr_layout(prec, m, n, t, want_q != 0, 0, &total);
+    return total;
+}
+
+size_t mdls_backsub_workspace(int prec, int64_t n, int tile) {
+    int t = norm_tile(tile, n);
+    if (!prec_ok(prec) || t < 1 || n < 1) return 0;
+    size_t total = 0;
+    bs_layout(prec, n, t, &total);
+    return total;
+}
+
+size_t mdls_lstsq_workspace(int prec, int64_t m, int64_t n, int tile, int mode) {
+    int t = norm_tile(tile, n);
+    if (!prec_ok(prec) || t < 1 || m < n || n < 1 || mode != MDLS_MODE_PLAIN) return 0;
+    return ls_layout(prec, m, n, t).total;
+}
+
+int mdls_qr(int prec, int64_t m, int64_t n, double* A, int64_t lda, int64_t psa, double* Q,
+            int64_t ldq, int64_t psq, int tile, int mode, void* ws, size_t ws_bytes, void* stream) {
+    if (!prec_ok(prec)) return MDLS_ERR_PREC;
+    if (mode != MDLS_MODE_PLAIN) return MDLS_ERR_ARG;
+    if (!A || n < 1 || m < n || lda < m || psa < lda * n) return MDLS_ERR_ARG;
+    if (Q && (ldq < m || psq < ldq * m)) return MDLS_ERR_ARG;
+    const int t = norm_tile(tile, n);
+    if (t < 1) return MDLS_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, mdls_qr_workspace(prec, m, n, tile, Q != nullptr, mode)))
+        return MDLS_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (prec) {
+        case 2: return qr_entry_p2(m, n, A, lda, psa, Q, ldq, psq, t, ws, st);
+        case 4: return qr_entry_p4(m, n, A, lda, psa, Q, ldq, psq, t, ws, st);
+        default: return qr_entry_p8(m, n, A, lda, psa, Q, ldq, psq, t, ws, st);
+    }
+}
+
+int mdls_backsub(int prec, int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y,
+                 int64_t psy, double* x, int64_t psx, int tile, void* ws, size_t ws_bytes,
+                 void* stream) {
+    if (!prec_ok(prec)) return MDLS_ERR_PREC;
+    if (!R || !y || !x || n < 1 || ldr < n || psr < ldr * n || psy < n || psx < n)
+        return MDLS_ERR_ARG;
+    const int t = norm_tile(tile, n);
+    if (t < 1) return MDLS_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, mdls_backsub_workspace(prec, n, tile))) return MDLS_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (prec) {
+        case 2: return bs_entry_p2(n, R, ldr, psr, y, psy, x, psx, t, ws, st);
+        case 4: return bs_entry_p4(n, R, ldr, psr, y, psy, x, psx, t, ws, st);
+        default: return bs_entry_p8(n, R, ldr, psr, y, psy, x, psx, t, ws, st);
+    }
+}
+
+int mdls_lstsq(int prec, int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa,
+               const double* b, int64_t psb, double* x, int64_t psx, int tile, int mode, void* ws,
+               size_t ws_bytes, void* stream) {
+    if (!prec_ok(prec)) return MDLS_ERR_PREC;
+    if (mode != MDLS_MODE_PLAIN) return MDLS_ERR_ARG;
+    if (!A || !b || !x || n < 1 || m < n || lda < m || psa < lda * n || psb < m || psx < n)
+        return MDLS_ERR_ARG;
+    const int t = norm_tile(tile, n);
+    if (t < 1) return MDLS_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, mdls_lstsq_workspace(prec, m, n, tile, mode))) return MDLS_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (prec) {
+        case 2: return ls_entry_p2(m, n, A, lda, psa, b, psb, x, psx, t, ws, st);
+        case 4: return ls_entry_p4(m, n, A, lda, psa, b, psb, x, psx, t, ws, st);
+        default: return ls_entry_p8(m, n, A, lda, psa, b, psb, x, psx, t, ws, st);
+    }
+}
+
+int mdls_vec_op(int prec, int op, int64_t count, const double* a, int64_t psa, const double* b,
+                int64_t psb, double* c, int64_t psc, void* stream) {
+    if (!prec_ok(prec)) return MDLS_ERR_PREC;
+    if (op < MDLS_OP_ADD || op > MDLS_OP_SQRT || count < 0 || !a || !c || psa < count || psc < count)
+        return MDLS_ERR_ARG;
+    if (op != MDLS_OP_SQRT && (!b || psb < count)) return MDLS_ERR_ARG;
+    if (op == MDLS_OP_SQRT) { b = a; psb = psa; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (prec) {
+        case 2: return vec_entry_p2(op, count, a, psa, b, psb, c, psc, st);
+        case 4: return vec_entry_p4(op, count, a, psa, b, psb, c, psc, st);
+        default: return vec_entry_p8(op, count, a, psa, b, psb, c, psc, st);
+    }
+}
+
+int mdls_read_status(const void* ws, int* status, void* stream) {
+    if (!ws || !status) return MDLS_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MDLS_ERR_CUDA;
+    if (cudaMemcpy(status, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MDLS_ERR_CUDA;
+    return MDLS_OK;
+}
+
+}  // extern "C"

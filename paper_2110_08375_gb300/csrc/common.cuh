@@ -1,0 +1,89 @@
+// Shared device definitions: limb-planar matrix views and the workspace
+// header (device status word, failure flag of the bounded waits).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mdls.h"
+#include "md.cuh"
+
+namespace mdls {
+
+#define DEV_INLINE __device__ __forceinline__
+
+// Limb-planar storage ("staggered" storage of the paper's Section 2): limb l
+// of entry (i, j) sits at ptr[l * ps + j * ld + i].
+struct Dense {
+    double* ptr;
+    int64_t ld, ps;
+};
+
+template <int P>
+DEV_INLINE md<P> ld_md(const double* __restrict__ ptr, int64_t ps, int64_t off) {
+    md<P> r;
+#pragma unroll
+    for (int l = 0; l < P; ++l) r.v[l] = ptr[l * ps + off];
+    return r;
+}
+
+template <int P>
+DEV_INLINE void st_md(double* __restrict__ ptr, int64_t ps, int64_t off, const md<P>& x) {
+#pragma unroll
+    for (int l = 0; l < P; ++l) ptr[l * ps + off] = x.v[l];
+}
+
+// Operand views for the md GEMM.  get(i, k, l) returns limb l of element
+// (i, k) of the operand as the GEMM sees it.
+struct ViewDense {      // X(i, k)
+    const double* ptr;
+    int64_t ld, ps;
+    DEV_INLINE double get(int64_t i, int64_t k, int l) const { return ptr[l * ps + k * ld + i]; }
+};
+struct ViewDenseT {     // X(k, i): the transpose
+    const double* ptr;
+    int64_t ld, ps;
+    DEV_INLINE double get(int64_t i, int64_t k, int l) const { return ptr[l * ps + i * ld + k]; }
+};
+// Unit lower trapezoid Y of Householder vectors stored below the diagonal:
+// Y(i, k) = 0 for i < k, 1 for i == k, stored value for i > k.
+struct ViewTrap {
+    const double* ptr;  // points at the panel's (0, 0)
+    int64_t ld, ps;
+    DEV_INLINE double get(int64_t i, int64_t k, int l) const {
+        if (i > k) return ptr[l * ps + k * ld + i];
+        return (i == k && l == 0) ? 1.0 : 0.0;
+    }
+};
+struct ViewTrapT {      // Y^T
+    const double* ptr;
+    int64_t ld, ps;
+    DEV_INLINE double get(int64_t i, int64_t k, int l) const {
+        if (k > i) return ptr[l * ps + i * ld + k];
+        return (k == i && l == 0) ? 1.0 : 0.0;
+    }
+};
+// Upper triangular operand (entries below the diagonal read as zero).
+struct ViewUpper {
+    const double* ptr;
+    int64_t ld, ps;
+    DEV_INLINE double get(int64_t i, int64_t k, int l) const {
+        return (i <= k) ? ptr[l * ps + k * ld + i] : 0.0;
+    }
+};
+
+// ----------------------------------------------------------------------------
+// Workspace header: status word and grid-barrier state live at the start of
+// every workspace the caller hands in.
+// ----------------------------------------------------------------------------
+struct WsHeader {
+    int status;            // first error seen on the device (0 = none)
+    int pad0;
+    unsigned int pad1[2];
+    int bar_error;         // set by a bounded wait that gave up: later waits fail fast
+    int pad2[59];          // header is 256 bytes
+};
+static_assert(sizeof(WsHeader) == 256, "workspace header must be 256 bytes");
+
+DEV_INLINE void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+}  // namespace mdls

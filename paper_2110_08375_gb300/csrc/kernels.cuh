@@ -1,0 +1,353 @@
+// Kernels of the plain multiple-double path (FP64 CUDA cores), templated on
+// the limb count P.  Section and algorithm numbers refer to arXiv 2110.08375.
+#pragma once
+#include "common.cuh"
+
+namespace mdls {
+
+constexpr long long kFlagTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+template <int P>
+DEV_INLINE md<P> md_one() {
+    return md_from_double<P>(1.0);
+}
+
+// loads that bypass L1 (data written by other blocks of the same launch)
+template <int P>
+DEV_INLINE md<P> ld_md_cg(const double* ptr, int64_t ps, int64_t off) {
+    md<P> r;
+#pragma unroll
+    for (int l = 0; l < P; ++l) r.v[l] = __ldcg(ptr + l * ps + off);
+    return r;
+}
+
+// Deterministic block reduction (fixed binary tree), result in every thread.
+template <int P, int NT>
+DEV_INLINE md<P> block_sum(md<P> x, md<P>* red) {
+    const int tid = threadIdx.x;
+    red[tid] = x;
+    __syncthreads();
+#pragma unroll 1
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (tid < s) red[tid] = md_add<P>(red[tid], red[tid + s]);
+        __syncthreads();
+    }
+    md<P> r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// Waits (thread 0 only) until *flag == want.  Bounded: on timeout it records
+// MDLS_ERR_TIMEOUT and returns false.  Also returns false when another block
+// has already failed.
+DEV_INLINE bool wait_flag(const unsigned int* flag, unsigned int want, WsHeader* h) {
+    const volatile unsigned int* vf = flag;
+    const volatile int* verr = &h->bar_error;
+    long long t0 = clock64();
+    while (*vf != want) {
+        if (*verr) return false;
+        if (clock64() - t0 > kFlagTimeoutCycles) {
+            atomicExch(&h->bar_error, 1);
+            set_status(&h->status, MDLS_ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
+// ----------------------------------------------------------------------------
+// Panel factorisation: step 1 of Algorithm 2 ("for l = 1..n: compute v and
+// beta, update R_kk") for one tile of w columns and r rows.
+//
+// Block c owns panel column c.  For l = 0..c-1 it waits until column l's
+// Householder vector is published, then applies that reflector to its column
+// (w_c = beta v^T a_c, a_c -= v w_c: the paper's "beta R^T v" and "update R").
+// Its column is then final, so it computes its own Householder vector
+// ("beta, v", Golub & Van Loan Alg. 5.1.1 sign convention: P x = ||x|| e1),
+// stores v below the diagonal (v_0 = 1 implicit), beta and R_cc, and raises
+// its flag.  The reflector of column c+1 is thus computed as soon as column
+// c+1 has received reflector c, while the other blocks are still applying it.
+// All blocks are co-resident (cooperative launch) and every wait is bounded.
+// ----------------------------------------------------------------------------
+struct PanelArgs {
+    double* A;            // working matrix
+    int64_t ld, ps;
+    int64_t j0;           // panel origin: global row = global column = j0
+    int64_t r;            // rows of the panel (m - j0)
+    int w;                // columns of the panel
+    double* beta;         // w md values, plane stride beta_ps
+    int64_t beta_ps;
+    unsigned int* flags;  // w flags
+    unsigned int epoch;   // flag value meaning "ready" for this panel
+    WsHeader* hdr;
+};
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) panel_kernel(PanelArgs a) {
+    const int c = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int64_t ld = a.ld, ps = a.ps;
+    double* base = a.A + a.j0 * ld + a.j0;  // panel (0, 0)
+    double* colc = base + (int64_t)c * ld;
+    __shared__ md<P> red[NT];
+    __shared__ md<P> sh_scal[3];  // beta, 1/v0, R_cc
+    __shared__ int sh_flag;
+
+    for (int ell = 0; ell < c; ++ell) {
+        if (tid == 0) sh_flag = wait_flag(a.flags + ell, a.epoch, a.hdr) ? 1 : 0;
+        __syncthreads();
+        const int ready = sh_flag;
+        __syncthreads();  // every thread has read sh_flag before it is reused
+        if (!ready) return;
+        const md<P> beta = ld_md_cg<P>(a.beta, a.beta_ps, ell);
+        if (beta.v[0] == 0.0) continue;  // identity reflector (uniform branch)
+        const double* v = base + (int64_t)ell * ld;
+        md<P> s = md_zero<P>();
+        for (int64_t i = ell + tid; i < a.r; i += NT) {
+            md<P> vi = (i == ell) ? md_one<P>() : ld_md_cg<P>(v, ps, i);
+            s = md_fma<P>(s, vi, ld_md<P>(colc, ps, i));
+        }
+        s = block_sum<P, NT>(s, red);
+        const md<P> wc = md_mul<P>(beta, s);
+        for (int64_t i = ell + tid; i < a.r; i += NT) {
+            md<P> vi = (i == ell) ? md_one<P>() : ld_md_cg<P>(v, ps, i);
+            st_md<P>(colc, ps, i, md_fms<P>(ld_md<P>(colc, ps, i), vi, wc));
+        }
+        __syncthreads();
+    }
+
+    // Householder vector of column c (rows c..r-1)
+    md<P> sig = md_zero<P>();
+    for (int64_t i = c + 1 + tid; i < a.r; i += NT) {
+        md<P> xi = ld_md<P>(colc, ps, i);
+        sig = md_fma<P>(sig, xi, xi);
+    }
+    sig = block_sum<P, NT>(sig, red);
+    if (tid == 0) {
+        md<P> x0 = ld_md<P>(colc, ps, c);
+        md<P> beta, inv, rcc;
+        int kind;  // 0 general, 1 identity, 2 flip e1
+        if (sig.v[0] == 0.0) {
+            if (x0.v[0] >= 0.0) {
+                kind = 1; beta = md_zero<P>(); rcc = x0;
+            } else {
+                kind = 2; beta = md_from_double<P>(2.0); rcc = md_neg<P>(x0);
+            }
+            inv = md_zero<P>();
+        } else {
+            kind = 0;
+            md<P> mu = md_sqrt<P>(md_fma<P>(sig, x0, x0));
+            md<P> v0;
+            if (x0.v[0] <= 0.0) v0 = md_sub<P>(x0, mu);
+            else v0 = md_neg<P>(md_div<P>(sig, md_add<P>(x0, mu)));  // -sigma/(x0+mu)
+            md<P> v0sq = md_mul<P>(v0, v0);
+            beta = md_scale<P>(md_div<P>(v0sq, md_add<P>(sig, v0sq)), 2.0);
+            inv = md_div<P>(md_one<P>(), v0);
+            rcc = mu;
+        }
+        sh_scal[0] = beta;
+        sh_scal[1] = inv;
+        sh_scal[2] = rcc;
+        sh_flag = kind;
+    }
+    __syncthreads();
+    if (sh_flag == 0) {
+        const md<P> inv = sh_scal[1];
+        for (int64_t i = c + 1 + tid; i < a.r; i += NT)
+            st_md<P>(colc, ps, i, md_mul<P>(ld_md<P>(colc, ps, i), inv));
+    }
+    if (tid == 0) {
+        st_md<P>(colc, ps, c, sh_scal[2]);
+        st_md<P>(a.beta, a.beta_ps, c, sh_scal[0]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        atomicExch(a.flags + c, a.epoch);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// md GEMM: C(i,j) = [C(i,j)] +/- sum_k A(i,k) B(k,j), one output per thread,
+// 16x16 output tile per block, operands staged limb-planar in shared memory.
+// Used for every product of the WY representation (Section 3):
+// G = Y^T Y, W = -Y T, W^T C, C + Y (W^T C), Y^T Q, Q + W (Y^T Q).
+// ----------------------------------------------------------------------------
+constexpr int kGemmTile = 16;
+
+template <int P, class AV, class BV>
+__global__ void __launch_bounds__(kGemmTile* kGemmTile)
+    gemm_kernel(int64_t M, int64_t N, int64_t K, AV A, BV B, Dense C, int negate, int accumulate) {
+    __shared__ double As[P][kGemmTile][kGemmTile + 1];
+    __shared__ double Bs[P][kGemmTile][kGemmTile + 1];
+    const int tx = threadIdx.x % kGemmTile, ty = threadIdx.x / kGemmTile;
+    const int64_t i0 = (int64_t)blockIdx.x * kGemmTile, j0 = (int64_t)blockIdx.y * kGemmTile;
+    const int64_t i = i0 + tx, j = j0 + ty;
+    md<P> acc = md_zero<P>();
+    for (int64_t k0 = 0; k0 < K; k0 += kGemmTile) {
+        const bool a_in = (i0 + tx < M) && (k0 + ty < K);
+        const bool b_in = (k0 + tx < K) && (j0 + ty < N);
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            As[l][ty][tx] = a_in ? A.get(i0 + tx, k0 + ty, l) : 0.0;   // A(i0+tx, k0+ty)
+            Bs[l][ty][tx] = b_in ? B.get(k0 + tx, j0 + ty, l) : 0.0;   // B(k0+tx, j0+ty)
+        }
+        __syncthreads();
+        const int kmax = (int)((K - k0) < kGemmTile ? (K - k0) : kGemmTile);
+        for (int kk = 0; kk < kmax; ++kk) {
+            md<P> av, bv;
+#pragma unroll
+            for (int l = 0; l < P; ++l) {
+                av.v[l] = As[l][kk][tx];
+                bv.v[l] = Bs[l][ty][kk];
+            }
+            acc = md_fma<P>(acc, av, bv);
+        }
+        __syncthreads();
+    }
+    if (i < M && j < N) {
+        if (negate) acc = md_neg<P>(acc);
+        const int64_t off = j * C.ld + i;
+        if (accumulate) acc = md_add<P>(ld_md<P>(C.ptr, C.ps, off), acc);
+        st_md<P>(C.ptr, C.ps, off, acc);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Inversion of upper triangular tiles: step 1 of Algorithm 1.  Block i
+// inverts diagonal tile i (rows/cols o..o+tt-1 of U); thread k solves
+// U v = e_k for column k of the inverse (back substitution with the
+// reciprocals of the diagonal computed once per tile).  A zero pivot records
+// MDLS_ERR_SINGULAR.  The inverse is written upper triangular with zeros
+// below the diagonal, tile i at D + i * dtile, column-major with ld dld.
+// ----------------------------------------------------------------------------
+template <int P>
+__global__ void tri_inv_kernel(const double* U, int64_t ld, int64_t ps, int64_t n, int t,
+                               double* D, int64_t dld, int64_t dps, int64_t dtile,
+                               WsHeader* hdr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    md<P>* inv_diag = reinterpret_cast<md<P>*>(smem_raw);
+    const int64_t o = (int64_t)blockIdx.x * t;
+    const int tt = (int)((n - o) < t ? (n - o) : t);
+    const int k = threadIdx.x;
+    const double* Ut = U + o * ld + o;
+    if (k < tt) {
+        md<P> d = ld_md<P>(Ut, ps, (int64_t)k * ld + k);
+        if (d.v[0] == 0.0) {
+            set_status(&hdr->status, MDLS_ERR_SINGULAR);
+            inv_diag[k] = md_zero<P>();
+        } else {
+            inv_diag[k] = md_div<P>(md_one<P>(), d);
+        }
+    }
+    __syncthreads();
+    if (k >= t) return;
+    double* col = D + blockIdx.x * dtile + (int64_t)k * dld;
+    if (k < tt) {
+        st_md<P>(col, dps, k, inv_diag[k]);
+        for (int l = k - 1; l >= 0; --l) {
+            md<P> s = md_zero<P>();
+            for (int q = l + 1; q <= k; ++q)
+                s = md_fma<P>(s, ld_md<P>(Ut, ps, (int64_t)q * ld + l), ld_md<P>(col, dps, q));
+            st_md<P>(col, dps, l, md_neg<P>(md_mul<P>(s, inv_diag[l])));
+        }
+        for (int l = k + 1; l < t; ++l) st_md<P>(col, dps, l, md_zero<P>());
+    } else {
+        for (int l = 0; l < t; ++l) st_md<P>(col, dps, l, md_zero<P>());
+    }
+}
+
+// T of the WY representation of one tile.  With G = Y^T Y and the betas of
+// the panel, T_jj = beta_j and T[l, j] = -beta_j sum_{q=l}^{j-1} T[l, q] G[q, j]
+// for l < j, so that H_1 ... H_w = I - Y T Y^T = I + W Y^T with W = -Y T.
+// Column j of W is then z_j = -beta_j (v_j + W_{:,<j} (Y_{:,<j}^T v_j)): the
+// paper's formula for z (Section 3), with the products Y^T v read from G.
+// Row l of T depends only on its own earlier entries: thread l builds it.
+// An identity reflector (beta_j = 0) gives a zero column j, as it must.
+template <int P>
+__global__ void wy_t_kernel(const double* G, int64_t ldg, int64_t psg, const double* beta,
+                            int64_t bps, int w, double* T, int64_t ldt, int64_t pst) {
+    const int l = threadIdx.x;
+    if (l >= w) return;
+    st_md<P>(T, pst, (int64_t)l * ldt + l, ld_md<P>(beta, bps, l));
+    for (int j = l + 1; j < w; ++j) {
+        md<P> s = md_zero<P>();
+        for (int q = l; q < j; ++q)
+            s = md_fma<P>(s, ld_md<P>(T, pst, (int64_t)q * ldt + l), ld_md<P>(G, psg, (int64_t)j * ldg + q));
+        st_md<P>(T, pst, (int64_t)j * ldt + l, md_neg<P>(md_mul<P>(ld_md<P>(beta, bps, j), s)));
+    }
+}
+
+// Step 2(a) of Algorithm 1: x_i := U_i^{-1} b_i (one block, thread k computes
+// entry k; the inverse tile is upper triangular).
+template <int P>
+__global__ void bs_mulinv_kernel(const double* Dt, int64_t dld, int64_t dps, int tt,
+                                 const double* bw, int64_t bps, double* x, int64_t xps,
+                                 int64_t o) {
+    const int k = threadIdx.x;
+    if (k >= tt) return;
+    md<P> s = md_zero<P>();
+    for (int q = k; q < tt; ++q)
+        s = md_fma<P>(s, ld_md<P>(Dt, dps, (int64_t)q * dld + k), ld_md<P>(bw, bps, o + q));
+    st_md<P>(x, xps, o + k, s);
+}
+
+// Step 2(b) of Algorithm 1: b_j := b_j - A_{j,i} x_i for all rows above tile
+// i at once (thread per row).
+template <int P>
+__global__ void bs_update_kernel(const double* U, int64_t ld, int64_t ps, int64_t o, int tt,
+                                 const double* x, int64_t xps, double* bw, int64_t bps) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= o) return;
+    md<P> s = ld_md<P>(bw, bps, row);
+    const double* Ur = U + o * ld + row;
+    for (int q = 0; q < tt; ++q) s = md_fms<P>(s, ld_md<P>(Ur, ps, (int64_t)q * ld), ld_md<P>(x, xps, o + q));
+    st_md<P>(bw, bps, row, s);
+}
+
+// Elementwise md arithmetic (mdls_vec_op).
+template <int P>
+__global__ void vec_op_kernel(int op, int64_t count, const double* a, int64_t psa, const double* b,
+                              int64_t psb, double* c, int64_t psc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const md<P> x = ld_md<P>(a, psa, i);
+    md<P> r;
+    switch (op) {
+        case MDLS_OP_ADD: r = md_add<P>(x, ld_md<P>(b, psb, i)); break;
+        case MDLS_OP_SUB: r = md_sub<P>(x, ld_md<P>(b, psb, i)); break;
+        case MDLS_OP_MUL: r = md_mul<P>(x, ld_md<P>(b, psb, i)); break;
+        case MDLS_OP_DIV: r = md_div<P>(x, ld_md<P>(b, psb, i)); break;
+        case MDLS_OP_FMA: r = md_fma<P>(ld_md<P>(c, psc, i), x, ld_md<P>(b, psb, i)); break;
+        default: r = md_sqrt<P>(x); break;
+    }
+    st_md<P>(c, psc, i, r);
+}
+
+// R output: zero the strictly lower part (rows > col) of an m x n matrix.
+template <int P>
+__global__ void zero_lower_kernel(double* A, int64_t ld, int64_t ps, int64_t m, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        if (i < m && i > j) {
+#pragma unroll
+            for (int l = 0; l < P; ++l) A[l * ps + j * ld + i] = 0.0;
+        }
+    }
+}
+
+// Q := I (m x m)
+template <int P>
+__global__ void identity_kernel(double* Q, int64_t ld, int64_t ps, int64_t m) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t j = blockIdx.y; j < m; j += gridDim.y) {
+        if (i < m) {
+#pragma unroll
+            for (int l = 0; l < P; ++l) Q[l * ps + j * ld + i] = (l == 0 && i == j) ? 1.0 : 0.0;
+        }
+    }
+}
+
+}  // namespace mdls

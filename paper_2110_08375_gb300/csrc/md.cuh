@@ -1,0 +1,353 @@
+// Multiple-double arithmetic on the FP64 CUDA cores (device code).
+//
+// A multiple double (arXiv 2110.08375, Section 1.1) is an unevaluated sum of
+// P doubles, most significant first: P = 2 double double, 4 quad double,
+// 8 octo double.  As in the paper's implementation notes (Section 4.1) a value
+// lives in P separate registers, never in an array in memory.
+//
+// Building blocks are the error-free transforms
+//   two_sum   (Knuth):  s + e == a + b exactly,
+//   two_prod  (FMA):    p + e == a * b exactly (no underflow),
+// written with explicit round-to-nearest intrinsics so that the compiler can
+// neither contract nor reassociate them.
+//
+// add / mul / fused multiply-add use one scheme for every P ("bins by order"):
+// each term of the exact result has a nominal order d (a_i*b_j has order i+j,
+// the low half of a two_prod one order more, limb c_d of an addend order d).
+// Bin d (d < P-1) is summed with two_sum, every rounding error going on to bin
+// d+1 as a new term; bin P-1 is summed with plain additions and FMAs, whose
+// errors are of order P and are dropped.  The P bin sums are then renormalised
+// (a bottom-up then a top-down two_sum sweep).  The absolute error is a small
+// multiple of 2^(-53P) (|a||b| + |c|), the bound used by the normwise error
+// analysis of Householder QR; the result limbs decrease by about 2^-53 each.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace mdls {
+
+// Host compilation (unit tests of the arithmetic on the CPU) uses plain IEEE
+// operations; the host compiler must not contract them (-ffp-contract=off).
+#define MD_INLINE __host__ __device__ __forceinline__
+
+template <int P>
+struct md {
+    double v[P];
+};
+
+#ifdef __CUDA_ARCH__
+MD_INLINE double dadd(double a, double b) { return __dadd_rn(a, b); }
+MD_INLINE double dsub(double a, double b) { return __dsub_rn(a, b); }
+MD_INLINE double dmul(double a, double b) { return __dmul_rn(a, b); }
+MD_INLINE double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+MD_INLINE double dnan() { return __longlong_as_double(0x7ff8000000000000LL); }
+#else
+inline double dadd(double a, double b) { return a + b; }
+inline double dsub(double a, double b) { return a - b; }
+inline double dmul(double a, double b) { return a * b; }
+inline double dfma(double a, double b, double c) { return ::fma(a, b, c); }
+inline double dnan() { return __builtin_nan(""); }
+#endif
+
+// Knuth's TwoSum (6 flops): s = fl(a+b), e = (a+b) - s exactly.
+MD_INLINE void two_sum(double a, double b, double& s, double& e) {
+    double x = dadd(a, b);
+    double bb = dsub(x, a);
+    e = dadd(dsub(a, dsub(x, bb)), dsub(b, bb));
+    s = x;
+}
+
+// TwoProd with FMA (2 flops): p = fl(ab), e = ab - p exactly.
+MD_INLINE void two_prod(double a, double b, double& p, double& e) {
+    double x = dmul(a, b);
+    e = dfma(a, b, -x);
+    p = x;
+}
+
+template <int P>
+MD_INLINE md<P> md_zero() {
+    md<P> r;
+#pragma unroll
+    for (int i = 0; i < P; ++i) r.v[i] = 0.0;
+    return r;
+}
+
+template <int P>
+MD_INLINE md<P> md_from_double(double x) {
+    md<P> r = md_zero<P>();
+    r.v[0] = x;
+    return r;
+}
+
+template <int P>
+MD_INLINE md<P> md_neg(const md<P>& a) {
+    md<P> r;
+#pragma unroll
+    for (int i = 0; i < P; ++i) r.v[i] = -a.v[i];
+    return r;
+}
+
+// multiplication by a power of two (exact barring under/overflow)
+template <int P>
+MD_INLINE md<P> md_scale(const md<P>& a, double pow2) {
+    md<P> r;
+#pragma unroll
+    for (int i = 0; i < P; ++i) r.v[i] = dmul(a.v[i], pow2);
+    return r;
+}
+
+MD_INLINE bool nonzero(double x) {
+#ifdef __CUDA_ARCH__
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) != 0;  // integer test, not the FP64 pipe
+#else
+    return x != 0.0;
+#endif
+}
+
+// Renormalisation of K terms of (roughly) decreasing order into P limbs.
+// 1. A bottom-up two_sum sweep moves the total towards s[0] (exact).
+// 2. A top-down two_sum sweep emits a limb each time the running sum leaves
+//    a nonzero error, and otherwise carries the sum on.  Zero terms are thus
+//    skipped: after heavy cancellation the bins can sum to zero in front of
+//    nonzero lower terms, and the result must still start with a nonzero
+//    leading limb and have no zero limb in front of a nonzero one.  Limb
+//    slots are written with selects, so everything stays in registers.
+// Terms beyond the P-th emitted limb are of order P and are dropped.
+template <int K, int P>
+MD_INLINE md<P> renorm_n(double (&s)[K]) {
+#pragma unroll
+    for (int i = K - 2; i >= 0; --i) two_sum(s[i], s[i + 1], s[i], s[i + 1]);
+    md<P> y;
+#pragma unroll
+    for (int k = 0; k < P; ++k) y.v[k] = 0.0;
+    int j = 0;
+    double e = s[0];
+#pragma unroll
+    for (int i = 1; i < K; ++i) {
+        double r, e2;
+        two_sum(e, s[i], r, e2);
+        const bool emit = nonzero(e2);
+#pragma unroll
+        for (int k = 0; k < P; ++k) y.v[k] = (emit && j == k) ? r : y.v[k];
+        j += emit ? 1 : 0;
+        e = emit ? e2 : r;
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) y.v[k] = (j == k) ? e : y.v[k];
+    return y;
+}
+
+template <int P>
+MD_INLINE md<P> renorm(double (&s)[P]) {
+    return renorm_n<P, P>(s);
+}
+
+// Bin D of a fused multiply-add c + a*b (WC: with addend c) or a product:
+// receives c_D (WC), the high halves of the D+1 products a_i b_{D-i}, the D
+// low halves of the order D-1 products (lo_prev) and the NE two_sum errors
+// of bin D-1 (err_prev).  Bins below P-1 are summed with two_sum and pass
+// their errors on; bin P-1 is summed with plain FMAs and additions.
+// Template recursion keeps every array size and index a compile-time
+// constant, so all terms stay in registers.
+template <int P, bool WC, int D, int NE>
+struct FmaBin {
+    static constexpr int NLO = D;
+    static constexpr int NTERMS = (WC ? 1 : 0) + (D + 1) + NLO + NE;
+    static constexpr int NOUT = NTERMS - 1;
+    MD_INLINE static void run(const md<P>& c, const md<P>& a, const md<P>& b,
+                              const double (&lo_prev)[NLO > 0 ? NLO : 1],
+                              const double (&err_prev)[NE > 0 ? NE : 1], double (&s)[P]) {
+        if constexpr (D < P - 1) {
+            double lo_cur[D + 1];
+            double err_cur[NOUT > 0 ? NOUT : 1];
+            int ne = 0;
+            double acc;
+            bool have = WC;
+            if constexpr (WC) acc = c.v[D];
+            else acc = 0.0;
+#pragma unroll
+            for (int i = 0; i <= D; ++i) {
+                double hi, lo;
+                two_prod(a.v[i], b.v[D - i], hi, lo);
+                lo_cur[i] = lo;
+                if (have) {
+                    two_sum(acc, hi, acc, err_cur[ne]);
+                    ++ne;
+                } else {
+                    acc = hi;
+                    have = true;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NLO; ++i) {
+                two_sum(acc, lo_prev[i], acc, err_cur[ne]);
+                ++ne;
+            }
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                two_sum(acc, err_prev[k], acc, err_cur[ne]);
+                ++ne;
+            }
+            s[D] = acc;
+            FmaBin<P, WC, D + 1, NOUT>::run(c, a, b, lo_cur, err_cur, s);
+        } else {
+            double acc;
+            if constexpr (WC) acc = c.v[D];
+            else acc = 0.0;
+#pragma unroll
+            for (int i = 0; i <= D; ++i) acc = dfma(a.v[i], b.v[D - i], acc);
+#pragma unroll
+            for (int i = 0; i < NLO; ++i) acc = dadd(acc, lo_prev[i]);
+#pragma unroll
+            for (int k = 0; k < NE; ++k) acc = dadd(acc, err_prev[k]);
+            s[D] = acc;
+        }
+    }
+};
+
+template <int P, bool WC>
+MD_INLINE md<P> md_fma_impl(const md<P>& c, const md<P>& a, const md<P>& b) {
+    double s[P];
+    const double none[1] = {0.0};
+    FmaBin<P, WC, 0, 0>::run(c, a, b, none, none, s);
+    return renorm<P>(s);
+}
+
+template <int P>
+MD_INLINE md<P> md_fma(const md<P>& c, const md<P>& a, const md<P>& b) {
+    return md_fma_impl<P, true>(c, a, b);
+}
+
+template <int P>
+MD_INLINE md<P> md_mul(const md<P>& a, const md<P>& b) {
+    return md_fma_impl<P, false>(a, a, b);
+}
+
+// c - a*b
+template <int P>
+MD_INLINE md<P> md_fms(const md<P>& c, const md<P>& a, const md<P>& b) {
+    return md_fma_impl<P, true>(c, md_neg(a), b);
+}
+
+// Bin D of a + b: a_D, b_D and the NE errors of bin D-1.
+template <int P, int D, int NE>
+struct AddBin {
+    static constexpr int NOUT = NE + 1;
+    MD_INLINE static void run(const md<P>& a, const md<P>& b, const double (&err_prev)[NE > 0 ? NE : 1],
+                              double (&s)[P]) {
+        if constexpr (D < P - 1) {
+            double err_cur[NOUT];
+            double acc;
+            two_sum(a.v[D], b.v[D], acc, err_cur[0]);
+#pragma unroll
+            for (int k = 0; k < NE; ++k) two_sum(acc, err_prev[k], acc, err_cur[k + 1]);
+            s[D] = acc;
+            AddBin<P, D + 1, NOUT>::run(a, b, err_cur, s);
+        } else {
+            double acc = dadd(a.v[D], b.v[D]);
+#pragma unroll
+            for (int k = 0; k < NE; ++k) acc = dadd(acc, err_prev[k]);
+            s[D] = acc;
+        }
+    }
+};
+
+template <int P>
+MD_INLINE md<P> md_add(const md<P>& a, const md<P>& b) {
+    double s[P];
+    const double none[1] = {0.0};
+    AddBin<P, 0, 0>::run(a, b, none, s);
+    return renorm<P>(s);
+}
+
+template <int P>
+MD_INLINE md<P> md_sub(const md<P>& a, const md<P>& b) {
+    return md_add<P>(a, md_neg(b));
+}
+
+// Bin D of c + q*b for a double q: c_D, high half of q*b_D, low half of
+// q*b_{D-1}, and the NE errors of bin D-1.
+template <int P, int D, int NE>
+struct FmaDBin {
+    static constexpr int NOUT = NE + 1 + (D > 0 ? 1 : 0);
+    MD_INLINE static void run(const md<P>& c, double q, const md<P>& b, double lo_prev,
+                              const double (&err_prev)[NE > 0 ? NE : 1], double (&s)[P]) {
+        if constexpr (D < P - 1) {
+            double err_cur[NOUT];
+            double hi, lo, acc;
+            two_prod(q, b.v[D], hi, lo);
+            two_sum(c.v[D], hi, acc, err_cur[0]);
+            int ne = 1;
+            if constexpr (D > 0) {
+                two_sum(acc, lo_prev, acc, err_cur[ne]);
+                ++ne;
+            }
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                two_sum(acc, err_prev[k], acc, err_cur[ne]);
+                ++ne;
+            }
+            s[D] = acc;
+            FmaDBin<P, D + 1, NOUT>::run(c, q, b, lo, err_cur, s);
+        } else {
+            double acc = dfma(q, b.v[D], c.v[D]);
+            if constexpr (D > 0) acc = dadd(acc, lo_prev);
+#pragma unroll
+            for (int k = 0; k < NE; ++k) acc = dadd(acc, err_prev[k]);
+            s[D] = acc;
+        }
+    }
+};
+
+// c + q*b for a double q: products q*b_d have order d.
+template <int P>
+MD_INLINE md<P> md_fma_d(const md<P>& c, double q, const md<P>& b) {
+    double s[P];
+    const double none[1] = {0.0};
+    FmaDBin<P, 0, 0>::run(c, q, b, 0.0, none, s);
+    return renorm<P>(s);
+}
+
+// a / b by long division: quotient digit q_k = r_k / b_0 (one double
+// division), exact-ish remainder r_{k+1} = r_k - q_k b in md arithmetic,
+// P+1 digits, then the digits (each ~2^-52 below the previous) are
+// renormalised to P limbs.
+template <int P>
+MD_INLINE md<P> md_div(const md<P>& a, const md<P>& b) {
+    double q[P + 1];
+    md<P> r = a;
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+        q[k] = r.v[0] / b.v[0];
+        if (k < P) r = md_fma_d<P>(r, -q[k], b);
+    }
+    return renorm_n<P + 1, P>(q);
+}
+
+// sqrt(a) for a >= 0: x <- x + (a - x^2) / (2 x_0), each step gaining about
+// 53 bits, from the double square root of the leading limb.  Zero for a == 0,
+// NaN limbs for a < 0.
+template <int P>
+MD_INLINE md<P> md_sqrt(const md<P>& a) {
+    if (a.v[0] == 0.0) return md_zero<P>();
+    if (!(a.v[0] > 0.0)) {
+        md<P> r;
+#pragma unroll
+        for (int i = 0; i < P; ++i) r.v[i] = dnan();
+        return r;
+    }
+    md<P> x = md_from_double<P>(sqrt(a.v[0]));
+#pragma unroll
+    for (int it = 0; it < P; ++it) {
+        md<P> r = md_fms<P>(a, x, x);
+        double d = r.v[0] / dmul(2.0, x.v[0]);
+        md<P> dd = md_from_double<P>(d);
+        x = md_add<P>(x, dd);
+    }
+    return x;
+}
+
+MD_INLINE bool md_is_zero_top(double top) { return top == 0.0; }
+
+}  // namespace mdls

@@ -1,0 +1,133 @@
+"""Operation counts: the flop convention of every TFLOPS figure.
+
+Table 1 of arXiv 2110.08375 (Section 1.1) gives the double-precision operation
+count of one md add, mul and div; the paper converts per-kernel tallies of md
+operations to flops with these multipliers.  Here the md operations tallied
+are those of the UNBLOCKED Householder algorithm (the method's plain
+definition, column by column), so the blocked algorithm's extra work (the WY
+matrices, inverted diagonal tiles) earns no credit.  A square root counts as
+one division; a subtraction as one addition.
+
+Also here: the FP64 instruction and flop counts of one device md operation as
+the kernels implement them (csrc/md.cuh, "bins by order"), used for the FP64
+roofline.  FLOPs count an FMA as 2.
+"""
+from __future__ import annotations
+
+TABLE1_SIGMA = {2: {"add": 20, "mul": 23, "div": 70},
+                4: {"add": 89, "mul": 336, "div": 893},
+                8: {"add": 269, "mul": 1742, "div": 5126}}
+
+
+def table1_flops(p: int, counts: dict) -> int:
+    t = TABLE1_SIGMA[p]
+    return (counts.get("add", 0) * t["add"] + counts.get("mul", 0) * t["mul"]
+            + (counts.get("div", 0) + counts.get("sqrt", 0)) * t["div"])
+
+
+def qr_counts(m: int, n: int, want_q: bool = False, extra_cols: int = 0) -> dict:
+    """md operations of unblocked Householder QR of an m x n matrix, applied
+    also to ``extra_cols`` right-hand sides, Q accumulated when ``want_q``.
+
+    Column j (L = m - j rows): sigma = sum of squares, L-1 mul + L-1 add; when
+    L > 1 the reflector (mu, v0, beta, v) costs 2 mul + 3 add + 1 sqrt + L div
+    (the extra division of the x0 > 0 branch is not counted); applying it to
+    one column costs 2L+1 mul + 2L add.  The last column of a square matrix
+    (L = 1) has no reflector.
+    """
+    add = mul = dv = sq = 0
+    for j in range(n):
+        L = m - j
+        mul += L - 1
+        add += L - 1
+        if L == 1:
+            continue
+        mul += 2
+        add += 3
+        sq += 1
+        dv += L
+        cols = (n - j - 1) + extra_cols + ((m - j) if want_q else 0)
+        mul += cols * (2 * L + 1)
+        add += cols * (2 * L)
+    return {"add": add, "mul": mul, "div": dv, "sqrt": sq}
+
+
+def backsub_counts(n: int) -> dict:
+    """Row-by-row back substitution: n(n-1)/2 mul and add, n div."""
+    return {"add": n * (n - 1) // 2, "mul": n * (n - 1) // 2, "div": n, "sqrt": 0}
+
+
+def lstsq_counts(m: int, n: int) -> dict:
+    """QR of [A | b] (no Q) followed by back substitution."""
+    q = qr_counts(m, n, want_q=False, extra_cols=1)
+    b = backsub_counts(n)
+    return {k: q[k] + b[k] for k in q}
+
+
+def lstsq_table1_flops(p: int, m: int, n: int) -> int:
+    return table1_flops(p, lstsq_counts(m, n))
+
+
+# ---------------------------------------------------------------------------
+# FP64 cost of one device md operation (csrc/md.cuh)
+# ---------------------------------------------------------------------------
+TWO_SUM = (6, 6)      # (instructions, flops)
+TWO_PROD = (2, 3)     # DMUL + DFMA
+DFMA = (1, 2)
+DADD = (1, 1)
+
+
+def _add(a, b, k=1):
+    return (a[0] + k * b[0], a[1] + k * b[1])
+
+
+def renorm_cost(p: int):
+    n = (p - 1) + (p - 2 if p > 2 else 0)
+    return (n * TWO_SUM[0], n * TWO_SUM[1])
+
+
+def fma_cost(p: int, with_c: bool = True):
+    """(FP64 instructions, FP64 flops) of md c + a*b (with_c) or a*b."""
+    cost = (0, 0)
+    ne = 0
+    for d in range(p):
+        nlo = d
+        if d < p - 1:
+            nterms = (1 if with_c else 0) + (d + 1) + nlo + ne
+            cost = _add(cost, TWO_PROD, d + 1)
+            cost = _add(cost, TWO_SUM, nterms - 1)
+            ne = nterms - 1
+        else:
+            cost = _add(cost, DFMA, d + 1)
+            cost = _add(cost, DADD, nlo + ne)
+    return _add(cost, renorm_cost(p))
+
+
+def add_cost(p: int):
+    cost = (0, 0)
+    ne = 0
+    for d in range(p):
+        if d < p - 1:
+            cost = _add(cost, TWO_SUM, 1 + ne)
+            ne += 1
+        else:
+            cost = _add(cost, DADD, 1 + ne)
+    return _add(cost, renorm_cost(p))
+
+
+def gemm_md_fmas(M: int, N: int, K: int) -> int:
+    """md FMAs of one M x N x K product (one per output per k)."""
+    return M * N * K
+
+
+def trailing_md_fmas(m: int, n: int, t: int, extra_cols: int = 0) -> int:
+    """md FMAs of the trailing updates X = W^T C (w x nc x r) and
+    C += Y X (r x nc x w) over all tiles of a blocked QR."""
+    total = 0
+    for j0 in range(0, n, t):
+        w = min(t, n - j0)
+        r = m - j0
+        nc = n + extra_cols - (j0 + w)
+        if nc > 0:
+            total += 2 * w * nc * r
+    return total
