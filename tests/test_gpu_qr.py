@@ -69,3 +69,25 @@ def test_qr_special_cases_exact():
     mdls.mdls_qr(Ad, Qd, tile=2)
     assert np.array_equal(to_host(Ad)[0], np.diag([3.0, 2.0, 0.5]))
     assert np.array_equal(to_host(Qd)[0], np.diag([-1.0, 1.0, -1.0]))
+
+
+@pytest.mark.parametrize("p", [2, 8])
+def test_tall_skinny_uses_split_k(p):
+    """A tall, narrow QR: every product has a small output grid and a long K,
+    so the GEMMs run split-K (partials summed in a fixed order); R and Q must
+    still match the oracle, and two runs must agree bitwise."""
+    import torch
+    import paper_2110_08375_gb300 as mdls
+    m, n, tile = 700, 24, 8
+    A, _ = synth.lstsq_problem(p, m, n, seed=9, tag="qrtest")
+    outs = []
+    for _ in range(2):
+        Ad = to_dev(A)
+        Qd = torch.zeros((p, m, m), dtype=torch.float64, device="cuda")
+        ws = mdls.mdls_qr(Ad, Qd, tile=tile)
+        assert mdls.mdls_read_status(ws) == 0
+        outs.append((to_host(Ad), to_host(Qd)))
+    Rr, Qr, _ = oracle.qr(A)
+    assert oracle.rel_err(outs[0][0], Rr) < TOL[p]
+    assert oracle.rel_err(outs[0][1], Qr) < TOL[p]
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
