@@ -19,14 +19,62 @@ constexpr int panel_threads() {
         if (cudaGetLastError() != cudaSuccess) return MDLS_ERR_CUDA; \
     } while (0)
 
+inline int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// Scratch for split-K partial sums (cap md values per plane).
+struct SplitBuf {
+    double* ptr;
+    int64_t cap;
+};
+
+// Launches one md GEMM.  When the output grid alone would leave SMs idle,
+// the K range is split over grid.z (at most 16 ways, partials in `sb`) and a
+// reduction kernel adds the partials in a fixed order.
 template <int P, class AV, class BV>
-int launch_gemm(int stage, cudaStream_t st, int64_t M, int64_t N, int64_t K, AV a, BV b, Dense c,
-                bool neg, bool acc) {
+int launch_gemm(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t N, int64_t K, AV a, BV b,
+                Dense c, bool neg, bool acc, bool upper_only = false) {
     if (M <= 0 || N <= 0) return MDLS_OK;
     StageScope sc(stage, st);
-    dim3 grid((unsigned)((M + kGemmTile - 1) / kGemmTile), (unsigned)((N + kGemmTile - 1) / kGemmTile));
-    gemm_kernel<P, AV, BV><<<grid, kGemmTile * kGemmTile, 0, st>>>(M, N, K, a, b, c, neg ? 1 : 0,
-                                                                    acc ? 1 : 0);
+    const int64_t gx = (M + kGemmTile - 1) / kGemmTile, gy = (N + kGemmTile - 1) / kGemmTile;
+    const int64_t tiles = upper_only ? (gx * (gx + 1)) / 2 : gx * gy;
+    const int64_t target = 2 * (int64_t)sm_count();
+    int64_t S = 1;
+    if (tiles < target && K >= 4 * kGemmTile && sb.ptr != nullptr) {
+        S = (target + tiles - 1) / tiles;
+        if (S > 16) S = 16;
+        if (S > K / (2 * kGemmTile)) S = K / (2 * kGemmTile);
+        while (S > 1 && S * M * N > sb.cap) --S;
+    }
+    int64_t kchunk = K;
+    if (S > 1) {
+        kchunk = (K + S - 1) / S;
+        kchunk = (kchunk + kGemmTile - 1) / kGemmTile * kGemmTile;
+        S = (K + kchunk - 1) / kchunk;
+    }
+    if (K <= 0) kchunk = 1;
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)S);
+    if (S == 1) {
+        gemm_kernel<P, AV, BV><<<grid, kGemmTile * kGemmTile, 0, st>>>(
+            M, N, K, a, b, c, neg ? 1 : 0, acc ? 1 : 0, kchunk, 0, upper_only ? 1 : 0);
+        MDLS_LAUNCH_CHECK();
+        return MDLS_OK;
+    }
+    Dense part{sb.ptr, M, sb.cap};
+    gemm_kernel<P, AV, BV><<<grid, kGemmTile * kGemmTile, 0, st>>>(M, N, K, a, b, part, 0, 0, kchunk,
+                                                                    M * N, upper_only ? 1 : 0);
+    MDLS_LAUNCH_CHECK();
+    const int64_t total = M * N;
+    split_reduce_kernel<P><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(
+        M, N, (int)S, sb.ptr, M, sb.cap, M * N, c, neg ? 1 : 0, acc ? 1 : 0);
     MDLS_LAUNCH_CHECK();
     return MDLS_OK;
 }
@@ -63,6 +111,7 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
     double* X = reinterpret_cast<double*>(ws + L.X);
     double* Wb = reinterpret_cast<double*>(ws + L.W);
     unsigned int* flags = reinterpret_cast<unsigned int*>(ws + L.flags);
+    const SplitBuf sb{reinterpret_cast<double*>(ws + L.split), L.split_cap};
     const int64_t tt2 = (int64_t)t * t;
     const int64_t psx = (int64_t)t * L.xcols;
     const int64_t ldw = m;
@@ -89,23 +138,23 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
         const double* Yp = A + j0 * lda + j0;
         ViewTrap Y{Yp, lda, psa};
         ViewTrapT Yt{Yp, lda, psa};
-        int rc = launch_gemm<P>(ST_W, st, w, w, r, Yt, Y, Dense{G, t, tt2}, false, false);
+        int rc = launch_gemm<P>(ST_W, st, sb, w, w, r, Yt, Y, Dense{G, t, tt2}, false, false, true);
         if (rc) return rc;
         {
             StageScope sc(ST_W, st);
-            wy_t_kernel<P><<<1, w, 0, st>>>(G, t, tt2, beta, t, w, T, t, tt2);
+            wy_t_kernel<P><<<(unsigned)((w + 3) / 4), 128, 0, st>>>(G, t, tt2, beta, t, w, T, t, tt2);
             MDLS_LAUNCH_CHECK();
         }
         double* Wk = want_q ? (Wb + j0 * ldw + j0) : Wb;
-        rc = launch_gemm<P>(ST_W, st, r, w, w, Y, ViewUpper{T, t, tt2}, Dense{Wk, ldw, psw}, true, false);
+        rc = launch_gemm<P>(ST_W, st, sb, r, w, w, Y, ViewUpper{T, t, tt2}, Dense{Wk, ldw, psw}, true, false);
         if (rc) return rc;
         // 3. trailing update C := C + Y (W^T C)
         if (nc > 0) {
             double* Cp = A + (j0 + w) * lda + j0;
-            rc = launch_gemm<P>(ST_TRAIL, st, w, nc, r, ViewDenseT{Wk, ldw, psw}, ViewDense{Cp, lda, psa},
+            rc = launch_gemm<P>(ST_TRAIL, st, sb, w, nc, r, ViewDenseT{Wk, ldw, psw}, ViewDense{Cp, lda, psa},
                                 Dense{X, t, psx}, false, false);
             if (rc) return rc;
-            rc = launch_gemm<P>(ST_TRAIL, st, r, nc, w, Y, ViewDense{X, t, psx}, Dense{Cp, lda, psa}, false, true);
+            rc = launch_gemm<P>(ST_TRAIL, st, sb, r, nc, w, Y, ViewDense{X, t, psx}, Dense{Cp, lda, psa}, false, true);
             if (rc) return rc;
         }
     }
@@ -124,10 +173,10 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
             const double* Yp = A + j0 * lda + j0;
             double* Qs = Q + j0 * ldq + j0;
             double* Wk = Wb + j0 * ldw + j0;
-            int rc = launch_gemm<P>(ST_QACC, st, w, r, r, ViewTrapT{Yp, lda, psa}, ViewDense{Qs, ldq, psq},
+            int rc = launch_gemm<P>(ST_QACC, st, sb, w, r, r, ViewTrapT{Yp, lda, psa}, ViewDense{Qs, ldq, psq},
                                     Dense{X, t, psx}, false, false);
             if (rc) return rc;
-            rc = launch_gemm<P>(ST_QACC, st, r, r, w, ViewDense{Wk, ldw, psw}, ViewDense{X, t, psx},
+            rc = launch_gemm<P>(ST_QACC, st, sb, r, r, w, ViewDense{Wk, ldw, psw}, ViewDense{X, t, psx},
                                 Dense{Qs, ldq, psq}, false, true);
             if (rc) return rc;
         }
@@ -158,8 +207,8 @@ int bs_run(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y
     // step 1: invert the N diagonal tiles (N blocks of t threads)
     {
         StageScope sc(ST_INV, st);
-        tri_inv_kernel<P><<<(unsigned)N, t, t * sizeof(md<P>), st>>>(R, ldr, psr, n, t, D, t, dps,
-                                                                      tt2, hdr);
+        tri_inv_kernel<P><<<(unsigned)((N * t + 3) / 4), 128, 0, st>>>(R, ldr, psr, n, t, N, D, t,
+                                                                         dps, tt2, hdr);
         MDLS_LAUNCH_CHECK();
     }
     // step 2: i = N..1

@@ -37,6 +37,22 @@ DEV_INLINE md<P> block_sum(md<P> x, md<P>* red) {
     return r;
 }
 
+// Deterministic warp reduction: a fixed shfl_down tree ending in lane 0,
+// whose sum is then broadcast, so every lane gets the same bits.
+template <int P>
+DEV_INLINE md<P> warp_sum(md<P> x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        md<P> y;
+#pragma unroll
+        for (int l = 0; l < P; ++l) y.v[l] = __shfl_down_sync(0xffffffffu, x.v[l], off);
+        x = md_add<P>(x, y);
+    }
+#pragma unroll
+    for (int l = 0; l < P; ++l) x.v[l] = __shfl_sync(0xffffffffu, x.v[l], 0);
+    return x;
+}
+
 // Waits (thread 0 only) until *flag == want.  Bounded: on timeout it records
 // MDLS_ERR_TIMEOUT and returns false.  Also returns false when another block
 // has already failed.
@@ -177,25 +193,33 @@ __global__ void __launch_bounds__(NT) panel_kernel(PanelArgs a) {
 // ----------------------------------------------------------------------------
 constexpr int kGemmTile = 16;
 
+// With split-K (gridDim.z > 1) block z sums k in [z kchunk, (z+1) kchunk) and
+// writes its raw partial sum to C.ptr + z * zstride (negate/accumulate are
+// then applied by split_reduce_kernel).  upper_only skips output tiles that
+// lie entirely below the diagonal (symmetric products).
 template <int P, class AV, class BV>
 __global__ void __launch_bounds__(kGemmTile* kGemmTile)
-    gemm_kernel(int64_t M, int64_t N, int64_t K, AV A, BV B, Dense C, int negate, int accumulate) {
+    gemm_kernel(int64_t M, int64_t N, int64_t K, AV A, BV B, Dense C, int negate, int accumulate,
+                int64_t kchunk, int64_t zstride, int upper_only) {
     __shared__ double As[P][kGemmTile][kGemmTile + 1];
     __shared__ double Bs[P][kGemmTile][kGemmTile + 1];
     const int tx = threadIdx.x % kGemmTile, ty = threadIdx.x / kGemmTile;
     const int64_t i0 = (int64_t)blockIdx.x * kGemmTile, j0 = (int64_t)blockIdx.y * kGemmTile;
     const int64_t i = i0 + tx, j = j0 + ty;
+    if (upper_only && i0 > j0 + kGemmTile - 1) return;  // whole block below the diagonal
+    const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+    const int64_t kend = (kbeg + kchunk) < K ? (kbeg + kchunk) : K;
     md<P> acc = md_zero<P>();
-    for (int64_t k0 = 0; k0 < K; k0 += kGemmTile) {
-        const bool a_in = (i0 + tx < M) && (k0 + ty < K);
-        const bool b_in = (k0 + tx < K) && (j0 + ty < N);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += kGemmTile) {
+        const bool a_in = (i0 + tx < M) && (k0 + ty < kend);
+        const bool b_in = (k0 + tx < kend) && (j0 + ty < N);
 #pragma unroll
         for (int l = 0; l < P; ++l) {
             As[l][ty][tx] = a_in ? A.get(i0 + tx, k0 + ty, l) : 0.0;   // A(i0+tx, k0+ty)
             Bs[l][ty][tx] = b_in ? B.get(k0 + tx, j0 + ty, l) : 0.0;   // B(k0+tx, j0+ty)
         }
         __syncthreads();
-        const int kmax = (int)((K - k0) < kGemmTile ? (K - k0) : kGemmTile);
+        const int kmax = (int)((kend - k0) < kGemmTile ? (kend - k0) : kGemmTile);
         for (int kk = 0; kk < kmax; ++kk) {
             md<P> av, bv;
 #pragma unroll
@@ -208,54 +232,83 @@ __global__ void __launch_bounds__(kGemmTile* kGemmTile)
         __syncthreads();
     }
     if (i < M && j < N) {
-        if (negate) acc = md_neg<P>(acc);
         const int64_t off = j * C.ld + i;
+        if (gridDim.z > 1) {
+            st_md<P>(C.ptr + blockIdx.z * zstride, C.ps, off, acc);
+            return;
+        }
+        if (negate) acc = md_neg<P>(acc);
         if (accumulate) acc = md_add<P>(ld_md<P>(C.ptr, C.ps, off), acc);
         st_md<P>(C.ptr, C.ps, off, acc);
     }
 }
 
+// C(i,j) = [C(i,j)] +/- sum_z partial_z(i,j), z in increasing order.
+template <int P>
+__global__ void split_reduce_kernel(int64_t M, int64_t N, int S, const double* part, int64_t pld,
+                                    int64_t pps, int64_t zstride, Dense C, int negate,
+                                    int accumulate) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= M * N) return;
+    const int64_t i = idx % M, j = idx / M;
+    md<P> acc = ld_md<P>(part, pps, j * pld + i);
+    for (int z = 1; z < S; ++z) acc = md_add<P>(acc, ld_md<P>(part + z * zstride, pps, j * pld + i));
+    if (negate) acc = md_neg<P>(acc);
+    const int64_t off = j * C.ld + i;
+    if (accumulate) acc = md_add<P>(ld_md<P>(C.ptr, C.ps, off), acc);
+    st_md<P>(C.ptr, C.ps, off, acc);
+}
+
 // ----------------------------------------------------------------------------
-// Inversion of upper triangular tiles: step 1 of Algorithm 1.  Block i
-// inverts diagonal tile i (rows/cols o..o+tt-1 of U); thread k solves
-// U v = e_k for column k of the inverse (back substitution with the
-// reciprocals of the diagonal computed once per tile).  A zero pivot records
-// MDLS_ERR_SINGULAR.  The inverse is written upper triangular with zeros
-// below the diagonal, tile i at D + i * dtile, column-major with ld dld.
+// Inversion of upper triangular tiles: step 1 of Algorithm 1.  Diagonal tile
+// i covers rows/cols o..o+tt-1 of U (o = i t).  Column k of its inverse
+// solves U v = e_k: v_k = 1/U_kk and, for l = k-1 down to 0,
+// v_l = -(sum_{s=l+1}^{k} U_ls v_s) / U_ll.  The paper gives each column to
+// one thread; here one warp solves one column, its lanes splitting each sum
+// (fixed-order reduction), and grid.x * blockDim/32 warps cover the N*t
+// columns.  A zero pivot records MDLS_ERR_SINGULAR.  The inverse is written
+// upper triangular with zeros below the diagonal, tile i at D + i * dtile,
+// column-major with leading dimension dld.
 // ----------------------------------------------------------------------------
 template <int P>
 __global__ void tri_inv_kernel(const double* U, int64_t ld, int64_t ps, int64_t n, int t,
-                               double* D, int64_t dld, int64_t dps, int64_t dtile,
+                               int64_t ntiles, double* D, int64_t dld, int64_t dps, int64_t dtile,
                                WsHeader* hdr) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    md<P>* inv_diag = reinterpret_cast<md<P>*>(smem_raw);
-    const int64_t o = (int64_t)blockIdx.x * t;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= ntiles * t) return;  // whole warp
+    const int64_t tile = gw / t;
+    const int k = (int)(gw % t);
+    const int64_t o = tile * t;
     const int tt = (int)((n - o) < t ? (n - o) : t);
-    const int k = threadIdx.x;
     const double* Ut = U + o * ld + o;
-    if (k < tt) {
-        md<P> d = ld_md<P>(Ut, ps, (int64_t)k * ld + k);
-        if (d.v[0] == 0.0) {
-            set_status(&hdr->status, MDLS_ERR_SINGULAR);
-            inv_diag[k] = md_zero<P>();
-        } else {
-            inv_diag[k] = md_div<P>(md_one<P>(), d);
-        }
+    double* col = D + tile * dtile + (int64_t)k * dld;
+    if (k >= tt) {
+        for (int l = lane; l < t; l += 32) st_md<P>(col, dps, l, md_zero<P>());
+        return;
     }
-    __syncthreads();
-    if (k >= t) return;
-    double* col = D + blockIdx.x * dtile + (int64_t)k * dld;
-    if (k < tt) {
-        st_md<P>(col, dps, k, inv_diag[k]);
-        for (int l = k - 1; l >= 0; --l) {
-            md<P> s = md_zero<P>();
-            for (int q = l + 1; q <= k; ++q)
-                s = md_fma<P>(s, ld_md<P>(Ut, ps, (int64_t)q * ld + l), ld_md<P>(col, dps, q));
-            st_md<P>(col, dps, l, md_neg<P>(md_mul<P>(s, inv_diag[l])));
+    for (int l = k + 1 + lane; l < t; l += 32) st_md<P>(col, dps, l, md_zero<P>());
+    if (lane == 0) {
+        md<P> d = ld_md<P>(Ut, ps, (int64_t)k * ld + k);
+        if (d.v[0] == 0.0) set_status(&hdr->status, MDLS_ERR_SINGULAR);
+        st_md<P>(col, dps, k, d.v[0] == 0.0 ? md_zero<P>() : md_div<P>(md_one<P>(), d));
+    }
+    __syncwarp();
+    for (int l = k - 1; l >= 0; --l) {
+        md<P> s = md_zero<P>();
+        for (int q = l + 1 + lane; q <= k; q += 32)
+            s = md_fma<P>(s, ld_md<P>(Ut, ps, (int64_t)q * ld + l), ld_md<P>(col, dps, q));
+        s = warp_sum<P>(s);
+        if (lane == 0) {
+            md<P> d = ld_md<P>(Ut, ps, (int64_t)l * ld + l);
+            if (d.v[0] == 0.0) {
+                set_status(&hdr->status, MDLS_ERR_SINGULAR);
+                st_md<P>(col, dps, l, md_zero<P>());
+            } else {
+                st_md<P>(col, dps, l, md_neg<P>(md_div<P>(s, d)));
+            }
         }
-        for (int l = k + 1; l < t; ++l) st_md<P>(col, dps, l, md_zero<P>());
-    } else {
-        for (int l = 0; l < t; ++l) st_md<P>(col, dps, l, md_zero<P>());
+        __syncwarp();
     }
 }
 
@@ -264,19 +317,25 @@ __global__ void tri_inv_kernel(const double* U, int64_t ld, int64_t ps, int64_t 
 // for l < j, so that H_1 ... H_w = I - Y T Y^T = I + W Y^T with W = -Y T.
 // Column j of W is then z_j = -beta_j (v_j + W_{:,<j} (Y_{:,<j}^T v_j)): the
 // paper's formula for z (Section 3), with the products Y^T v read from G.
-// Row l of T depends only on its own earlier entries: thread l builds it.
-// An identity reflector (beta_j = 0) gives a zero column j, as it must.
+// Row l of T depends only on its own earlier entries: one warp builds row l,
+// its lanes splitting the sum over q (fixed-order reduction).  An identity
+// reflector (beta_j = 0) gives a zero column j, as it must.
 template <int P>
 __global__ void wy_t_kernel(const double* G, int64_t ldg, int64_t psg, const double* beta,
                             int64_t bps, int w, double* T, int64_t ldt, int64_t pst) {
-    const int l = threadIdx.x;
-    if (l >= w) return;
-    st_md<P>(T, pst, (int64_t)l * ldt + l, ld_md<P>(beta, bps, l));
+    const int l = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (l >= w) return;  // whole warp
+    if (lane == 0) st_md<P>(T, pst, (int64_t)l * ldt + l, ld_md<P>(beta, bps, l));
+    __syncwarp();
     for (int j = l + 1; j < w; ++j) {
         md<P> s = md_zero<P>();
-        for (int q = l; q < j; ++q)
+        for (int q = l + lane; q < j; q += 32)
             s = md_fma<P>(s, ld_md<P>(T, pst, (int64_t)q * ldt + l), ld_md<P>(G, psg, (int64_t)j * ldg + q));
-        st_md<P>(T, pst, (int64_t)j * ldt + l, md_neg<P>(md_mul<P>(ld_md<P>(beta, bps, j), s)));
+        s = warp_sum<P>(s);
+        if (lane == 0)
+            st_md<P>(T, pst, (int64_t)j * ldt + l, md_neg<P>(md_mul<P>(ld_md<P>(beta, bps, j), s)));
+        __syncwarp();
     }
 }
 

@@ -19,8 +19,8 @@ struct Bump {
 };
 
 struct QrLayout {
-    size_t flags, flag_bytes, beta, G, T, X, W;
-    int64_t xcols, wcols;
+    size_t flags, flag_bytes, beta, G, T, X, W, split;
+    int64_t xcols, wcols, split_cap;
 };
 struct BsLayout {
     size_t D, b;
@@ -45,6 +45,8 @@ inline QrLayout qr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool w
     L.X = B.take(d * t * (size_t)L.xcols);
     L.wcols = want_q ? n : t;
     L.W = B.take(d * (size_t)m * (size_t)L.wcols);
+    L.split_cap = 16 * (int64_t)t * t;   // split-K partial sums, md values per plane
+    L.split = B.take(d * (size_t)L.split_cap);
     return L;
 }
 
