@@ -107,6 +107,35 @@ int mdls_backsub(int prec, int64_t n, const double* R, int64_t ldr, int64_t psr,
 size_t mdls_backsub_workspace(int prec, int64_t n, int tile);
 
 /*
+ * mdls_backsub_noalloc -- the same back substitution as mdls_backsub, for
+ * callers that cannot allocate device memory when they call: a plugin inside
+ * a host framework that owns all device memory through its own allocator, a
+ * real-time or embedded loop whose memory budget is fixed at start-up, or
+ * code that must not risk the implicit device synchronisation of cudaMalloc.
+ * The paper has no counterpart to this entry point.
+ *   It allocates nothing.  Its scratch (the inverted diagonal tiles, the
+ *   working right-hand side and a status word) is a fixed device array of
+ *   MDLS_BACKSUB_NOALLOC_MAX_BYTES inside the library, held by every GPU that
+ *   loads the library until the process exits.  Problems needing more
+ *   scratch than that (mdls_backsub_workspace(prec, n, tile) bytes; at tile
+ *   128 about n <= 8000 in dd, 3900 in qd, 1900 in od) are rejected with
+ *   MDLS_ERR_WORKSPACE before anything is enqueued.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any
+ *   stream capture.  Every call clears the status word itself.
+ *   All calls share the one array: calls that overlap on the GPU (other
+ *   streams, other host threads) race and corrupt each other's results.
+ *   Keep per-stage timing (mdls_profile_enable) off: it creates CUDA events.
+ *   status: NULL, or a DEVICE int that receives MDLS_OK or MDLS_ERR_SINGULAR
+ *   when the solve has run.
+ * Other arguments, layout and errors as for mdls_backsub.
+ */
+#define MDLS_BACKSUB_NOALLOC_MAX_BYTES (16u << 20)
+int mdls_backsub_noalloc(int prec, int64_t n, const double* R, int64_t ldr, int64_t psr,
+                         const double* y, int64_t psy, double* x, int64_t psx, int tile,
+                         int* status, void* stream);
+
+/*
  * mdls_lstsq -- least squares solution of A x = b (Section 1): the blocked QR
  * of Algorithm 2 applied to [A | b] (so Q^T b is formed by the same WY
  * updates and Q itself is never built), followed by Algorithm 1 on
