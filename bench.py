@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--precs", default="2,4,8")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-modes", action="store_true")
     return ap.parse_args()
 
 
@@ -320,6 +321,43 @@ def run_gpu(args):
         # the e2e answers match the device-resident answers
         for p in precs:
             assert torch.equal(xs_host[p], data[p][2].cpu())
+
+    # precision modes on the same workload: split (tensor-core WY products) and
+    # refine (dd factorisation + refinement); each timed like the main loop and
+    # compared with the plain solve (max |x_mode - x_plain| / max |x_plain|,
+    # differences of limbs summed in float64)
+    if not args.no_modes:
+        plain_x = {p: data[p][2].clone() for p in precs}
+        modes = {}
+        for mname, mcode, plist in (("split", mdls.MODE_SPLIT, precs),
+                                    ("refine", mdls.MODE_REFINE, [p for p in precs if p > 2])):
+            res = {}
+            for p in plist:
+                Ad, bd, _, _ = data[p]
+                xm = torch.zeros((p, n), dtype=torch.float64, device=dev)
+                wsm = mdls.workspace(mdls.mdls_lstsq_workspace(p, n, n, t, mcode), dev)
+                mdls.mdls_lstsq(Ad, bd, xm, tile=t, mode=mcode, ws=wsm)
+                torch.cuda.synchronize()
+                st = mdls.mdls_read_status(wsm)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                ms = 0.0
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0.record(stream)
+                    mdls.mdls_lstsq(Ad, bd, xm, tile=t, mode=mcode, ws=wsm)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                ms /= args.steps
+                diff = (xm - plain_x[p]).sum(dim=0).abs().max().item()
+                scale = plain_x[p][0].abs().max().item()
+                res[PREC_NAMES[p]] = {"ms": ms, "speedup_vs_plain": (per_prec_ms[p] / args.steps) / ms,
+                                      "table1_tflops": fl[p] / (ms / 1e3) / 1e12,
+                                      "rel_diff_vs_plain": diff / scale, "status": st}
+                del wsm
+            modes[mname] = res
+        out["modes"] = modes
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(128, precs)

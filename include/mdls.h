@@ -60,9 +60,12 @@ extern "C" {
 #define MDLS_ERR_CUDA (-5)        /* a kernel launch failed               */
 #define MDLS_ERR_TIMEOUT (-6)     /* device: a bounded wait gave up       */
 #define MDLS_ERR_UNSUPPORTED (-7) /* valid request this build cannot run  */
+#define MDLS_ERR_NOT_CONVERGED (-8) /* device: refinement short of target */
 
 /* arithmetic modes of the QR and least-squares calls */
-#define MDLS_MODE_PLAIN 0 /* all arithmetic in md on the FP64 CUDA cores */
+#define MDLS_MODE_PLAIN 0  /* all arithmetic in md on the FP64 CUDA cores */
+#define MDLS_MODE_SPLIT 1  /* WY products as exact bf16 digit products on the tensor cores */
+#define MDLS_MODE_REFINE 2 /* least squares only: factor in double double, refine in prec */
 
 /* Library version (major * 10000 + minor * 100 + patch). */
 int mdls_version(void);
@@ -77,7 +80,16 @@ const char* mdls_status_string(int code);
  *     each P x = ||x|| e1) and its strictly lower part is exactly zero.
  *   Q (m x m) receives the orthogonal factor with A = Q R when Q != NULL
  *     (Algorithm 2's output); ldq >= m, psq >= ldq * m.  Q must not overlap A.
- *   mode: MDLS_MODE_PLAIN.
+ *   mode: MDLS_MODE_PLAIN, or MDLS_MODE_SPLIT: every product of the WY form
+ *     (Y^T Y, W = -Y T, W^T C, C + Y X, and those of Q) is evaluated by
+ *     splitting each md entry, scaled by a power of two per row of the left
+ *     and per column of the right factor, into S = ceil((53 prec + 12) / 8)
+ *     base-256 digits (15 dd, 28 qd, 55 od) held exactly in bf16; the digit
+ *     products accumulate exactly in fp32 on the tensor cores and are
+ *     renormalised into prec limbs (error-free splitting of Ozaki, Ogita,
+ *     Oishi and Rump).  The panel, T, norms and beta stay in md on the FP64
+ *     cores.  Accuracy is normwise: about 2^(-53 prec) times the row and
+ *     column scales of each product, as for the plain md products.
  * Per tile of t columns: the Householder vectors of the tile, its WY form
  * (P = I + W Y^T), then the trailing update C := C + Y (W^T C).  Q is
  * accumulated backward from the identity, Q := P_k Q for k = N..1.
@@ -141,6 +153,13 @@ int mdls_backsub_noalloc(int prec, int64_t n, const double* R, int64_t ldr, int6
  * updates and Q itself is never built), followed by Algorithm 1 on
  * R x = (Q^T b)[0:n].  A (m x n, m >= n >= 1) and b (length m) are read
  * only; x (length n) is written.  The working copy of [A | b] lives in ws.
+ * mode MDLS_MODE_SPLIT: the QR of [A | b] with split products (see mdls_qr).
+ * mode MDLS_MODE_REFINE (prec 4 or 8; with prec 2 it is the plain solve):
+ *   factor A rounded to double double (its two leading limbs), solve in
+ *   dd, then refine: r = b - A x in prec limbs, d = R^{-1}(Q^T r)[0:n] in dd,
+ *   x = x + d in prec limbs -- 3 refinement steps for qd, 6 for od.  If the
+ *   last correction is not below 2^(53-53 prec) |x| (ill-conditioned A),
+ *   MDLS_ERR_NOT_CONVERGED is recorded in the workspace status.
  * Workspace: mdls_lstsq_workspace(prec, m, n, tile, mode) bytes.
  */
 int mdls_lstsq(int prec, int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa,
@@ -184,7 +203,8 @@ int mdls_read_status(const void* ws, int* status, void* stream);
  * (NULL to skip), resets them, and returns the number of stages (or a
  * negative status).  Stage indices: 0 panel, 1 compute W, 2 trailing update,
  * 3 Q accumulation, 4 invert diagonal tiles, 5 multiply with inverses,
- * 6 back substitution updates, 7 other; mdls_stage_name() names them.
+ * 6 back substitution updates, 7 other, 8 refinement; mdls_stage_name()
+ * names them.
  * The profiler is process-wide; timing is meant for one thread at a time.
  */
 void mdls_profile_enable(int on);

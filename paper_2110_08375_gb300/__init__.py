@@ -28,7 +28,10 @@ MDLS_ERR_SINGULAR = -4
 MDLS_ERR_CUDA = -5
 MDLS_ERR_TIMEOUT = -6
 MDLS_ERR_UNSUPPORTED = -7
+MDLS_ERR_NOT_CONVERGED = -8
 MODE_PLAIN = 0
+MODE_SPLIT = 1
+MODE_REFINE = 2
 OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "fma": 4, "sqrt": 5}
 
 _lib = None
@@ -203,9 +206,9 @@ def mdls_vec_op(op: str, a, b=None, c=None, stream=None):
     return c
 
 
-N_STAGES = 8
+N_STAGES = 9
 STAGE_KEYS = ("panel", "compute_w", "trailing", "q_accum", "invert_tiles", "mul_inverses",
-              "bs_update", "other")
+              "bs_update", "other", "refine")
 
 
 def mdls_profile_enable(on: bool = True) -> None:

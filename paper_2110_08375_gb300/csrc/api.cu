@@ -8,13 +8,15 @@
 namespace mdls {
 #define MDLS_DECLARE(P)                                                                           \
     int qr_entry_p##P(int64_t, int64_t, double*, int64_t, int64_t, double*, int64_t, int64_t, int, \
-                      void*, cudaStream_t);                                                        \
+                      int, void*, cudaStream_t);                                                   \
     int bs_entry_p##P(int64_t, const double*, int64_t, int64_t, const double*, int64_t, double*,  \
                       int64_t, int, void*, cudaStream_t);                                          \
     int ls_entry_p##P(int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t,  \
-                      double*, int64_t, int, void*, cudaStream_t);                                 \
+                      double*, int64_t, int, int, void*, cudaStream_t);                            \
     int vec_entry_p##P(int, int64_t, const double*, int64_t, const double*, int64_t, double*,     \
-                       int64_t, cudaStream_t);
+                       int64_t, cudaStream_t);                                                     \
+    int ls_refine_entry_p##P(int64_t, int64_t, const double*, int64_t, int64_t, const double*,    \
+                             int64_t, double*, int64_t, int, int, void*, cudaStream_t);
 MDLS_DECLARE(2)
 MDLS_DECLARE(4)
 MDLS_DECLARE(8)
@@ -42,15 +44,17 @@ const char* mdls_status_string(int code) {
         case MDLS_ERR_CUDA: return "CUDA launch or copy failed";
         case MDLS_ERR_TIMEOUT: return "a bounded device wait gave up";
         case MDLS_ERR_UNSUPPORTED: return "request not supported by this build or device";
+        case MDLS_ERR_NOT_CONVERGED: return "iterative refinement did not reach the target precision";
         default: return "unknown status";
     }
 }
 
 size_t mdls_qr_workspace(int prec, int64_t m, int64_t n, int tile, int want_q, int mode) {
     int t = norm_tile(tile, n);
-    if (!prec_ok(prec) || t < 1 || m < n || n < 1 || mode != MDLS_MODE_PLAIN) return 0;
+    if (!prec_ok(prec) || t < 1 || m < n || n < 1) return 0;
+    if (mode != MDLS_MODE_PLAIN && mode != MDLS_MODE_SPLIT) return 0;
     size_t total = 0;
-    qr_layout(prec, m, n, t, want_q != 0, 0, &total);
+    qr_layout(prec, m, n, t, want_q != 0, 0, &total, mode == MDLS_MODE_SPLIT);
     return total;
 }
 
@@ -62,16 +66,20 @@ size_t mdls_backsub_workspace(int prec, int64_t n, int tile) {
     return total;
 }
 
+static bool refine_mode(int prec, int mode) { return mode == MDLS_MODE_REFINE && prec > 2; }
+
 size_t mdls_lstsq_workspace(int prec, int64_t m, int64_t n, int tile, int mode) {
     int t = norm_tile(tile, n);
-    if (!prec_ok(prec) || t < 1 || m < n || n < 1 || mode != MDLS_MODE_PLAIN) return 0;
-    return ls_layout(prec, m, n, t).total;
+    if (!prec_ok(prec) || t < 1 || m < n || n < 1) return 0;
+    if (mode != MDLS_MODE_PLAIN && mode != MDLS_MODE_REFINE && mode != MDLS_MODE_SPLIT) return 0;
+    if (refine_mode(prec, mode)) return ref_layout(prec, m, n, t).total;
+    return ls_layout(prec, m, n, t, mode == MDLS_MODE_SPLIT).total;
 }
 
 int mdls_qr(int prec, int64_t m, int64_t n, double* A, int64_t lda, int64_t psa, double* Q,
             int64_t ldq, int64_t psq, int tile, int mode, void* ws, size_t ws_bytes, void* stream) {
     if (!prec_ok(prec)) return MDLS_ERR_PREC;
-    if (mode != MDLS_MODE_PLAIN) return MDLS_ERR_ARG;
+    if (mode != MDLS_MODE_PLAIN && mode != MDLS_MODE_SPLIT) return MDLS_ERR_ARG;
     if (!A || n < 1 || m < n || lda < m || psa < lda * n) return MDLS_ERR_ARG;
     if (Q && (ldq < m || psq < ldq * m)) return MDLS_ERR_ARG;
     const int t = norm_tile(tile, n);
@@ -80,9 +88,9 @@ int mdls_qr(int prec, int64_t m, int64_t n, double* A, int64_t lda, int64_t psa,
         return MDLS_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (prec) {
-        case 2: return qr_entry_p2(m, n, A, lda, psa, Q, ldq, psq, t, ws, st);
-        case 4: return qr_entry_p4(m, n, A, lda, psa, Q, ldq, psq, t, ws, st);
-        default: return qr_entry_p8(m, n, A, lda, psa, Q, ldq, psq, t, ws, st);
+        case 2: return qr_entry_p2(m, n, A, lda, psa, Q, ldq, psq, t, mode, ws, st);
+        case 4: return qr_entry_p4(m, n, A, lda, psa, Q, ldq, psq, t, mode, ws, st);
+        default: return qr_entry_p8(m, n, A, lda, psa, Q, ldq, psq, t, mode, ws, st);
     }
 }
 
@@ -107,17 +115,22 @@ int mdls_lstsq(int prec, int64_t m, int64_t n, const double* A, int64_t lda, int
                const double* b, int64_t psb, double* x, int64_t psx, int tile, int mode, void* ws,
                size_t ws_bytes, void* stream) {
     if (!prec_ok(prec)) return MDLS_ERR_PREC;
-    if (mode != MDLS_MODE_PLAIN) return MDLS_ERR_ARG;
+    if (mode != MDLS_MODE_PLAIN && mode != MDLS_MODE_REFINE && mode != MDLS_MODE_SPLIT)
+        return MDLS_ERR_ARG;
     if (!A || !b || !x || n < 1 || m < n || lda < m || psa < lda * n || psb < m || psx < n)
         return MDLS_ERR_ARG;
     const int t = norm_tile(tile, n);
     if (t < 1) return MDLS_ERR_ARG;
     if (!ws_ok(ws, ws_bytes, mdls_lstsq_workspace(prec, m, n, tile, mode))) return MDLS_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (refine_mode(prec, mode)) {
+        if (prec == 4) return ls_refine_entry_p4(m, n, A, lda, psa, b, psb, x, psx, t, 3, ws, st);
+        return ls_refine_entry_p8(m, n, A, lda, psa, b, psb, x, psx, t, 6, ws, st);
+    }
     switch (prec) {
-        case 2: return ls_entry_p2(m, n, A, lda, psa, b, psb, x, psx, t, ws, st);
-        case 4: return ls_entry_p4(m, n, A, lda, psa, b, psb, x, psx, t, ws, st);
-        default: return ls_entry_p8(m, n, A, lda, psa, b, psb, x, psx, t, ws, st);
+        case 2: return ls_entry_p2(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st);
+        case 4: return ls_entry_p4(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st);
+        default: return ls_entry_p8(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st);
     }
 }
 

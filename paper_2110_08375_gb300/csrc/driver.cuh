@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "split.cuh"
 #include "layout.h"
 #include "profile.h"
 
@@ -30,11 +31,54 @@ inline int sm_count() {
     return sms;
 }
 
-// Scratch for split-K partial sums (cap md values per plane).
+// Digit slices of the tensor-core split products (precision mode "split").
+struct TcBuf {
+    __nv_bfloat16* As;
+    __nv_bfloat16* Bs;
+    int* ea;
+    int* fb;
+    size_t as_cap, bs_cap;  // bf16 elements
+    int64_t sc_cap;         // ints in ea and in fb
+};
+
+// Scratch for split-K partial sums (cap md values per plane), and the
+// tensor-core slices when the split mode is on (tc != nullptr).
 struct SplitBuf {
     double* ptr;
     int64_t cap;
+    const TcBuf* tc = nullptr;
 };
+
+template <int P>
+void split_gemm_setup() {
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(split_gemm_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)split_gemm_smem<P>());
+        done = true;
+    }
+}
+
+// C = [C] +/- A B through the digit slices on the tensor cores.
+template <int P, class AV, class BV>
+int launch_split_gemm(int stage, cudaStream_t st, const TcBuf& tc, int64_t M, int64_t N, int64_t K,
+                      AV a, BV b, Dense c, bool neg, bool acc) {
+    constexpr int S = SplitCfg<P>::S;
+    const int64_t Kp = (K + kSplitTk - 1) / kSplitTk * kSplitTk;
+    split_gemm_setup<P>();
+    StageScope sc(stage, st);
+    split_rows_kernel<P, AV><<<(unsigned)((M * 32 + 255) / 256), 256, 0, st>>>(M, K, Kp, a, tc.As, tc.ea);
+    MDLS_LAUNCH_CHECK();
+    split_rows_kernel<P, ViewTranspose<BV>><<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(
+        N, K, Kp, ViewTranspose<BV>{b}, tc.Bs, tc.fb);
+    MDLS_LAUNCH_CHECK();
+    dim3 grid((unsigned)((M + kSplitTm - 1) / kSplitTm), (unsigned)((N + kSplitTn - 1) / kSplitTn));
+    split_gemm_kernel<P><<<grid, 256, split_gemm_smem<P>(), st>>>(M, N, Kp, tc.As, tc.Bs, tc.ea, tc.fb, c,
+                                                                 neg ? 1 : 0, acc ? 1 : 0);
+    MDLS_LAUNCH_CHECK();
+    (void)S;
+    return MDLS_OK;
+}
 
 // Launches one md GEMM.  When the output grid alone would leave SMs idle,
 // the K range is split over grid.z (at most 16 ways, partials in `sb`) and a
@@ -43,6 +87,13 @@ template <int P, class AV, class BV>
 int launch_gemm(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t N, int64_t K, AV a, BV b,
                 Dense c, bool neg, bool acc, bool upper_only = false) {
     if (M <= 0 || N <= 0) return MDLS_OK;
+    if (sb.tc != nullptr && K > 0) {
+        const int64_t Kp = (K + kSplitTk - 1) / kSplitTk * kSplitTk;
+        constexpr int S = SplitCfg<P>::S;
+        if ((size_t)S * M * Kp <= sb.tc->as_cap && (size_t)S * N * Kp <= sb.tc->bs_cap &&
+            M <= sb.tc->sc_cap && N <= sb.tc->sc_cap)
+            return launch_split_gemm<P>(stage, st, *sb.tc, M, N, K, a, b, c, neg, acc);
+    }
     StageScope sc(stage, st);
     const int64_t gx = (M + kGemmTile - 1) / kGemmTile, gy = (N + kGemmTile - 1) / kGemmTile;
     const int64_t tiles = upper_only ? (gx * (gx + 1)) / 2 : gx * gy;
@@ -102,7 +153,7 @@ int panel_capacity() {
 template <int P>
 int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa, double* Q,
            int64_t ldq, int64_t psq, int t, char* ws, const QrLayout& L, WsHeader* hdr,
-           bool zero_lower, cudaStream_t st) {
+           bool zero_lower, cudaStream_t st, bool keep_w = false) {
     constexpr int NT = panel_threads<P>();
     if (t > panel_capacity<P>()) return MDLS_ERR_UNSUPPORTED;
     double* beta = reinterpret_cast<double*>(ws + L.beta);
@@ -111,7 +162,14 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
     double* X = reinterpret_cast<double*>(ws + L.X);
     double* Wb = reinterpret_cast<double*>(ws + L.W);
     unsigned int* flags = reinterpret_cast<unsigned int*>(ws + L.flags);
-    const SplitBuf sb{reinterpret_cast<double*>(ws + L.split), L.split_cap};
+    TcBuf tcb{};
+    if (L.tc_as_cap > 0) {
+        tcb = TcBuf{reinterpret_cast<__nv_bfloat16*>(ws + L.tc_as), reinterpret_cast<__nv_bfloat16*>(ws + L.tc_bs),
+                    reinterpret_cast<int*>(ws + L.tc_ea), reinterpret_cast<int*>(ws + L.tc_fb),
+                    L.tc_as_cap, L.tc_bs_cap, L.tc_sc_cap};
+    }
+    const SplitBuf sb{reinterpret_cast<double*>(ws + L.split), L.split_cap,
+                      L.tc_as_cap > 0 ? &tcb : nullptr};
     const int64_t tt2 = (int64_t)t * t;
     const int64_t psx = (int64_t)t * L.xcols;
     const int64_t ldw = m;
@@ -133,7 +191,7 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
                 return MDLS_ERR_CUDA;
         }
         const int64_t nc = n + nextra - (j0 + w);  // trailing columns incl. right-hand sides
-        if (nc <= 0 && !want_q) continue;
+        if (nc <= 0 && !want_q && !keep_w) continue;
         // 2. WY form: G = Y^T Y, T from G and the betas, W = -Y T
         const double* Yp = A + j0 * lda + j0;
         ViewTrap Y{Yp, lda, psa};
@@ -145,7 +203,7 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
             wy_t_kernel<P><<<(unsigned)((w + 3) / 4), 128, 0, st>>>(G, t, tt2, beta, t, w, T, t, tt2);
             MDLS_LAUNCH_CHECK();
         }
-        double* Wk = want_q ? (Wb + j0 * ldw + j0) : Wb;
+        double* Wk = (want_q || keep_w) ? (Wb + j0 * ldw + j0) : Wb;
         rc = launch_gemm<P>(ST_W, st, sb, r, w, w, Y, ViewUpper{T, t, tt2}, Dense{Wk, ldw, psw}, true, false);
         if (rc) return rc;
         // 3. trailing update C := C + Y (W^T C)
@@ -191,10 +249,24 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
 }
 
 // Tiled back substitution (Algorithm 1) of R x = y, R upper triangular n x n.
+// Step 1: invert the N diagonal tiles into D.
 template <int P>
-int bs_run(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y, int64_t psy,
-           double* x, int64_t psx, int t, char* ws, const BsLayout& L, WsHeader* hdr,
-           cudaStream_t st) {
+int bs_invert(int64_t n, const double* R, int64_t ldr, int64_t psr, int t, char* ws,
+              const BsLayout& L, WsHeader* hdr, cudaStream_t st) {
+    const int64_t N = (n + t - 1) / t;
+    const int64_t tt2 = (int64_t)t * t;
+    double* D = reinterpret_cast<double*>(ws + L.D);
+    StageScope sc(ST_INV, st);
+    tri_inv_kernel<P><<<(unsigned)((N * t + 3) / 4), 128, 0, st>>>(R, ldr, psr, n, t, N, D, t,
+                                                                     N * tt2, tt2, hdr);
+    MDLS_LAUNCH_CHECK();
+    return MDLS_OK;
+}
+
+// Step 2: i = N..1, x_i := U_i^{-1} y_i, then y_j -= A_{j,i} x_i for all j < i.
+template <int P>
+int bs_solve(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y, int64_t psy,
+             double* x, int64_t psx, int t, char* ws, const BsLayout& L, cudaStream_t st) {
     const int64_t N = (n + t - 1) / t;
     const int64_t tt2 = (int64_t)t * t;
     double* D = reinterpret_cast<double*>(ws + L.D);
@@ -204,14 +276,6 @@ int bs_run(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y
         if (cudaMemcpyAsync(bw + l * n, y + l * psy, n * sizeof(double), cudaMemcpyDeviceToDevice,
                             st) != cudaSuccess)
             return MDLS_ERR_CUDA;
-    // step 1: invert the N diagonal tiles (N blocks of t threads)
-    {
-        StageScope sc(ST_INV, st);
-        tri_inv_kernel<P><<<(unsigned)((N * t + 3) / 4), 128, 0, st>>>(R, ldr, psr, n, t, N, D, t,
-                                                                         dps, tt2, hdr);
-        MDLS_LAUNCH_CHECK();
-    }
-    // step 2: i = N..1
     for (int64_t i = N - 1; i >= 0; --i) {
         const int64_t o = i * t;
         const int tt = (int)((n - o) < t ? (n - o) : t);
@@ -231,9 +295,94 @@ int bs_run(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y
 }
 
 template <int P>
+int bs_run(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y, int64_t psy,
+           double* x, int64_t psx, int t, char* ws, const BsLayout& L, WsHeader* hdr,
+           cudaStream_t st) {
+    int rc = bs_invert<P>(n, R, ldr, psr, t, ws, L, hdr, st);
+    if (rc) return rc;
+    return bs_solve<P>(n, R, ldr, psr, y, psy, x, psx, t, ws, L, st);
+}
+
+// v := Q^T v for the Q = P_1 ... P_N of a factorisation whose Y sit below the
+// diagonal of A (ld m) and whose W_k were kept (ld m, plane stride psw):
+// v[j0:] := v[j0:] + Y_k (W_k^T v[j0:]) for k = 1..N (each P_k^T = I + Y W^T).
+template <int P>
+int apply_qt(int64_t m, int64_t n, int t, const double* A, int64_t psa, const double* Wb,
+             int64_t psw, double* v, int64_t psv, double* X, int64_t psx, SplitBuf sb, int stage,
+             cudaStream_t st) {
+    const int64_t ntiles = (n + t - 1) / t;
+    for (int64_t k = 0; k < ntiles; ++k) {
+        const int64_t j0 = k * t;
+        const int w = (int)((n - j0) < t ? (n - j0) : t);
+        const int64_t r = m - j0;
+        const double* Wk = Wb + j0 * m + j0;
+        int rc = launch_gemm<P>(stage, st, sb, w, 1, r, ViewDenseT{Wk, m, psw}, ViewDense{v + j0, m, psv},
+                                Dense{X, t, psx}, false, false);
+        if (rc) return rc;
+        rc = launch_gemm<P>(stage, st, sb, r, 1, w, ViewTrap{A + j0 * m + j0, m, psa},
+                            ViewDense{X, t, psx}, Dense{v + j0, m, psv}, false, true);
+        if (rc) return rc;
+    }
+    return MDLS_OK;
+}
+
+// Solves R^T h = g (R upper triangular n x n, its diagonal tiles inverted in
+// L.D by bs_invert): the block forward substitution of the transposed system.
+template <int P>
+int fs_solve(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* g, int64_t psg,
+             double* h, int64_t psh, int t, char* ws, const BsLayout& L, int stage, cudaStream_t st) {
+    const int64_t N = (n + t - 1) / t;
+    const int64_t tt2 = (int64_t)t * t;
+    const double* D = reinterpret_cast<const double*>(ws + L.D);
+    double* gw = reinterpret_cast<double*>(ws + L.b);
+    for (int l = 0; l < P; ++l)
+        if (cudaMemcpyAsync(gw + l * n, g + l * psg, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess)
+            return MDLS_ERR_CUDA;
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t o = i * t;
+        const int tt = (int)((n - o) < t ? (n - o) : t);
+        {
+            StageScope sc(stage, st);
+            fs_mulinv_t_kernel<P><<<1, t, 0, st>>>(D + i * tt2, t, N * tt2, tt, gw, n, h, psh, o);
+            MDLS_LAUNCH_CHECK();
+        }
+        const int64_t rest = n - o - tt;
+        if (rest > 0) {
+            StageScope sc(stage, st);
+            fs_update_kernel<P><<<(unsigned)((rest + 127) / 128), 128, 0, st>>>(R, ldr, psr, o, tt, n, h,
+                                                                              psh, gw, n);
+            MDLS_LAUNCH_CHECK();
+        }
+    }
+    return MDLS_OK;
+}
+
+// v := Q v = P_1 (P_2 (... (P_N v))): v[j0:] := v[j0:] + W_k (Y_k^T v[j0:]), k = N..1.
+template <int P>
+int apply_q(int64_t m, int64_t n, int t, const double* A, int64_t psa, const double* Wb,
+            int64_t psw, double* v, int64_t psv, double* X, int64_t psx, SplitBuf sb, int stage,
+            cudaStream_t st) {
+    const int64_t ntiles = (n + t - 1) / t;
+    for (int64_t k = ntiles - 1; k >= 0; --k) {
+        const int64_t j0 = k * t;
+        const int w = (int)((n - j0) < t ? (n - j0) : t);
+        const int64_t r = m - j0;
+        const double* Wk = Wb + j0 * m + j0;
+        int rc = launch_gemm<P>(stage, st, sb, w, 1, r, ViewTrapT{A + j0 * m + j0, m, psa},
+                                ViewDense{v + j0, m, psv}, Dense{X, t, psx}, false, false);
+        if (rc) return rc;
+        rc = launch_gemm<P>(stage, st, sb, r, 1, w, ViewDense{Wk, m, psw}, ViewDense{X, t, psx},
+                            Dense{v + j0, m, psv}, false, true);
+        if (rc) return rc;
+    }
+    return MDLS_OK;
+}
+
+template <int P>
 int qr_entry(int64_t m, int64_t n, double* A, int64_t lda, int64_t psa, double* Q, int64_t ldq,
-             int64_t psq, int t, void* ws, cudaStream_t st) {
-    QrLayout L = qr_layout(P, m, n, t, Q != nullptr, 0);
+             int64_t psq, int t, int mode, void* ws, cudaStream_t st) {
+    QrLayout L = qr_layout(P, m, n, t, Q != nullptr, 0, nullptr, mode == MDLS_MODE_SPLIT);
     char* w = static_cast<char*>(ws);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(w);
     if (cudaMemsetAsync(w, 0, L.flags + L.flag_bytes, st) != cudaSuccess) return MDLS_ERR_CUDA;
@@ -252,8 +401,8 @@ int bs_entry(int64_t n, const double* R, int64_t ldr, int64_t psr, const double*
 
 template <int P>
 int ls_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa, const double* b,
-             int64_t psb, double* x, int64_t psx, int t, void* ws, cudaStream_t st) {
-    LsLayout L = ls_layout(P, m, n, t);
+             int64_t psb, double* x, int64_t psx, int t, int mode, void* ws, cudaStream_t st) {
+    LsLayout L = ls_layout(P, m, n, t, mode == MDLS_MODE_SPLIT);
     char* w = static_cast<char*>(ws);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(w);
     if (cudaMemsetAsync(w, 0, L.qr.flags + L.qr.flag_bytes, st) != cudaSuccess) return MDLS_ERR_CUDA;
@@ -282,22 +431,132 @@ int vec_entry(int op, int64_t count, const double* a, int64_t psa, const double*
     return MDLS_OK;
 }
 
+// Least squares in P limbs by double-double factorisation and iterative
+// refinement of the augmented system [I A; A^T 0][r; x] = [b; 0] (Bjorck's
+// refinement, which converges for inconsistent systems too).  The QR of A
+// rounded to dd (its two leading limbs) gives x0 and r0 = b - A x0; then,
+// `iters` times, with the residuals formed in P limbs
+//   f = b - r - A x,  g = -A^T r,
+// and the corrections solved in dd with the factors A = Q [R; 0]:
+//   [f1; f2] = Q^T f,  h = R^{-T} g,  dr = Q [h; f2],  dx = R^{-1} (f1 - h),
+// r := r + dr and x := x + dx in P limbs.  A last check records
+// MDLS_ERR_NOT_CONVERGED when the final |dx| exceeds 2^(53-53P) |x|.
+template <int P>
+int ls_refine_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa, const double* b,
+                    int64_t psb, double* x, int64_t psx, int t, int iters, void* ws, cudaStream_t st) {
+    RefLayout L = ref_layout(P, m, n, t);
+    char* w = static_cast<char*>(ws);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(w);
+    if (cudaMemsetAsync(w, 0, L.qr.flags + L.qr.flag_bytes, st) != cudaSuccess) return MDLS_ERR_CUDA;
+    double* A2 = reinterpret_cast<double*>(w + L.A2);
+    const int64_t ps2 = m * n;
+    double* res = reinterpret_cast<double*>(w + L.res);     // r, P limbs, length m
+    double* f = reinterpret_cast<double*>(w + L.f);         // f, P limbs, length m
+    double* g = reinterpret_cast<double*>(w + L.g);         // g, P limbs, length n
+    double* c = reinterpret_cast<double*>(w + L.c);         // dd, length m
+    double* hv = reinterpret_cast<double*>(w + L.h);        // dd, length n
+    double* dx = reinterpret_cast<double*>(w + L.d);        // dd, length n
+    double* up = reinterpret_cast<double*>(w + L.up);       // P limbs, length m (promoted corrections)
+    double* X = reinterpret_cast<double*>(w + L.qr.X);
+    const double* Wb = reinterpret_cast<const double*>(w + L.qr.W);
+    const int64_t psw = L.qr.wcols * m, psX = (int64_t)t * L.qr.xcols;
+    const SplitBuf sbP{reinterpret_cast<double*>(w + L.splitP), L.splitP_cap};
+    const SplitBuf sb2{reinterpret_cast<double*>(w + L.qr.split), L.qr.split_cap};
+    const size_t vb = sizeof(double);
+#define MDLS_CPY(dst, src, cnt) \
+    if (cudaMemcpyAsync((dst), (src), (cnt) * vb, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return MDLS_ERR_CUDA
+    for (int l = 0; l < 2; ++l)
+        if (cudaMemcpy2DAsync(A2 + l * ps2, m * vb, A + l * psa, lda * vb, m * vb, n,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return MDLS_ERR_CUDA;
+    int rc = qr_run<2>(m, n, 0, A2, m, ps2, nullptr, 0, 0, t, w, L.qr, hdr, false, st, true);
+    if (rc) return rc;
+    rc = bs_invert<2>(n, A2, m, ps2, t, w, L.bs, hdr, st);
+    if (rc) return rc;
+    if (cudaMemsetAsync(up, 0, (size_t)P * m * vb, st) != cudaSuccess) return MDLS_ERR_CUDA;
+    auto vec = [&](int op, int64_t cnt, const double* a, int64_t pa, const double* bb, int64_t pb, double* cc,
+                   int64_t pc) -> int {
+        StageScope sc(ST_REFINE, st);
+        vec_op_kernel<P><<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(op, cnt, a, pa, bb, pb, cc, pc);
+        MDLS_LAUNCH_CHECK();
+        return MDLS_OK;
+    };
+    auto vec2 = [&](int op, int64_t cnt, const double* a, int64_t pa, const double* bb, int64_t pb, double* cc,
+                    int64_t pc) -> int {
+        StageScope sc(ST_REFINE, st);
+        vec_op_kernel<2><<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(op, cnt, a, pa, bb, pb, cc, pc);
+        MDLS_LAUNCH_CHECK();
+        return MDLS_OK;
+    };
+    // x0 = R^{-1} (Q^T b)[0:n] in dd
+    for (int l = 0; l < 2; ++l) { MDLS_CPY(c + l * m, b + l * psb, m); }
+    if ((rc = apply_qt<2>(m, n, t, A2, ps2, Wb, psw, c, m, X, psX, sb2, ST_REFINE, st))) return rc;
+    if ((rc = bs_solve<2>(n, A2, m, ps2, c, m, dx, n, t, w, L.bs, st))) return rc;
+    for (int l = 0; l < P; ++l) {
+        if (l < 2) { MDLS_CPY(x + l * psx, dx + l * n, n); }
+        else if (cudaMemsetAsync(x + l * psx, 0, n * vb, st) != cudaSuccess) return MDLS_ERR_CUDA;
+    }
+    // r0 = b - A x0 in P limbs
+    for (int l = 0; l < P; ++l) { MDLS_CPY(res + l * m, b + l * psb, m); }
+    if ((rc = launch_gemm<P>(ST_REFINE, st, sbP, m, 1, n, ViewDense{A, lda, psa}, ViewDense{x, n, psx},
+                             Dense{res, m, m}, true, true)))
+        return rc;
+    for (int it = 0; it < iters; ++it) {
+        // f = b - r - A x,  g = -A^T r  (P limbs)
+        if ((rc = vec(MDLS_OP_SUB, m, b, psb, res, m, f, m))) return rc;
+        if ((rc = launch_gemm<P>(ST_REFINE, st, sbP, m, 1, n, ViewDense{A, lda, psa}, ViewDense{x, n, psx},
+                                 Dense{f, m, m}, true, true)))
+            return rc;
+        if ((rc = launch_gemm<P>(ST_REFINE, st, sbP, n, 1, m, ViewDenseT{A, lda, psa}, ViewDense{res, m, m},
+                                 Dense{g, n, n}, true, false)))
+            return rc;
+        // [f1; f2] = Q^T f (dd)
+        for (int l = 0; l < 2; ++l) { MDLS_CPY(c + l * m, f + l * m, m); }
+        if ((rc = apply_qt<2>(m, n, t, A2, ps2, Wb, psw, c, m, X, psX, sb2, ST_REFINE, st))) return rc;
+        // h = R^{-T} g (dd); dx = R^{-1} (f1 - h)
+        if ((rc = fs_solve<2>(n, A2, m, ps2, g, n, hv, n, t, w, L.bs, ST_REFINE, st))) return rc;
+        if ((rc = vec2(MDLS_OP_SUB, n, c, m, hv, n, dx, n))) return rc;   // dx <- f1 - h (temporarily)
+        // dr = Q [h; f2]: reuse c with its first n entries replaced by h
+        for (int l = 0; l < 2; ++l) { MDLS_CPY(c + l * m, hv + l * n, n); }
+        if ((rc = apply_q<2>(m, n, t, A2, ps2, Wb, psw, c, m, X, psX, sb2, ST_REFINE, st))) return rc;
+        for (int l = 0; l < 2; ++l) { MDLS_CPY(up + l * m, c + l * m, m); }
+        if ((rc = vec(MDLS_OP_ADD, m, res, m, up, m, res, m))) return rc;          // r += dr
+        if ((rc = bs_solve<2>(n, A2, m, ps2, dx, n, hv, n, t, w, L.bs, st))) return rc;  // hv <- R^{-1}(f1 - h)
+        for (int l = 0; l < 2; ++l) { MDLS_CPY(up + l * m, hv + l * n, n); }
+        if ((rc = vec(MDLS_OP_ADD, n, x, psx, up, m, x, psx))) return rc;         // x += dx
+        // keep dx for the convergence check
+        for (int l = 0; l < 2; ++l) { MDLS_CPY(dx + l * n, hv + l * n, n); }
+    }
+#undef MDLS_CPY
+    {
+        StageScope sc(ST_REFINE, st);
+        refine_check_kernel<<<1, 256, 0, st>>>(dx, n, x, n, 53 - 53 * P, hdr);
+        MDLS_LAUNCH_CHECK();
+    }
+    return MDLS_OK;
+}
+
 }  // namespace mdls
 
 #define MDLS_INSTANTIATE(P)                                                                       \
     namespace mdls {                                                                              \
     int qr_entry_p##P(int64_t m, int64_t n, double* A, int64_t lda, int64_t psa, double* Q,       \
-                      int64_t ldq, int64_t psq, int t, void* ws, cudaStream_t st) {               \
-        return qr_entry<P>(m, n, A, lda, psa, Q, ldq, psq, t, ws, st);                           \
+                      int64_t ldq, int64_t psq, int t, int mode, void* ws, cudaStream_t st) {     \
+        return qr_entry<P>(m, n, A, lda, psa, Q, ldq, psq, t, mode, ws, st);                     \
     }                                                                                             \
     int bs_entry_p##P(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y,      \
                       int64_t psy, double* x, int64_t psx, int t, void* ws, cudaStream_t st) {     \
         return bs_entry<P>(n, R, ldr, psr, y, psy, x, psx, t, ws, st);                           \
     }                                                                                             \
     int ls_entry_p##P(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa,            \
-                      const double* b, int64_t psb, double* x, int64_t psx, int t, void* ws,      \
-                      cudaStream_t st) {                                                          \
-        return ls_entry<P>(m, n, A, lda, psa, b, psb, x, psx, t, ws, st);                        \
+                      const double* b, int64_t psb, double* x, int64_t psx, int t, int mode,      \
+                      void* ws, cudaStream_t st) {                                                \
+        return ls_entry<P>(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st);                  \
+    }                                                                                             \
+    int ls_refine_entry_p##P(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa,     \
+                             const double* b, int64_t psb, double* x, int64_t psx, int t,         \
+                             int iters, void* ws, cudaStream_t st) {                              \
+        return ls_refine_entry<P>(m, n, A, lda, psa, b, psb, x, psx, t, iters, ws, st);          \
     }                                                                                             \
     int vec_entry_p##P(int op, int64_t count, const double* a, int64_t psa, const double* b,      \
                        int64_t psb, double* c, int64_t psc, cudaStream_t st) {                    \

@@ -353,6 +353,31 @@ __global__ void bs_mulinv_kernel(const double* Dt, int64_t dld, int64_t dps, int
     st_md<P>(x, xps, o + k, s);
 }
 
+// Forward substitution with R^T (lower triangular), using the same inverted
+// diagonal tiles: h_i := (U_i^{-1})^T g_i (thread k: sum over q <= k of
+// D(q, k) g(q)), then g_j := g_j - (R_ij)^T h_i for the rows after tile i.
+template <int P>
+__global__ void fs_mulinv_t_kernel(const double* Dt, int64_t dld, int64_t dps, int tt,
+                                   const double* gw, int64_t gps, double* h, int64_t hps, int64_t o) {
+    const int k = threadIdx.x;
+    if (k >= tt) return;
+    md<P> s = md_zero<P>();
+    for (int q = 0; q <= k; ++q)
+        s = md_fma<P>(s, ld_md<P>(Dt, dps, (int64_t)k * dld + q), ld_md<P>(gw, gps, o + q));
+    st_md<P>(h, hps, o + k, s);
+}
+
+template <int P>
+__global__ void fs_update_kernel(const double* U, int64_t ld, int64_t ps, int64_t o, int tt,
+                                 int64_t n, const double* h, int64_t hps, double* gw, int64_t gps) {
+    const int64_t row = o + tt + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    md<P> s = ld_md<P>(gw, gps, row);
+    const double* Ucol = U + row * ld + o;   // column `row` of R, rows o..o+tt-1
+    for (int q = 0; q < tt; ++q) s = md_fms<P>(s, ld_md<P>(Ucol, ps, q), ld_md<P>(h, hps, o + q));
+    st_md<P>(gw, gps, row, s);
+}
+
 // Step 2(b) of Algorithm 1: b_j := b_j - A_{j,i} x_i for all rows above tile
 // i at once (thread per row).
 template <int P>
@@ -383,6 +408,29 @@ __global__ void vec_op_kernel(int op, int64_t count, const double* a, int64_t ps
         default: r = md_sqrt<P>(x); break;
     }
     st_md<P>(c, psc, i, r);
+}
+
+// End of the refinement loop: MDLS_ERR_NOT_CONVERGED unless
+// max |d| <= 2^e2 max |x| (leading limbs; one block).
+static __global__ void refine_check_kernel(const double* d, int64_t n, const double* x, int64_t pad,
+                                    int e2, WsHeader* hdr) {
+    __shared__ double sd[256], sx[256];
+    double md = 0.0, mx = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        md = fmax(md, fabs(d[i]));
+        mx = fmax(mx, fabs(x[i]));
+    }
+    sd[threadIdx.x] = md;
+    sx[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + s]);
+            sx[threadIdx.x] = fmax(sx[threadIdx.x], sx[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && !(sd[0] <= ldexp(sx[0], e2))) set_status(&hdr->status, MDLS_ERR_NOT_CONVERGED);
 }
 
 // R output: zero the strictly lower part (rows > col) of an m x n matrix.

@@ -21,7 +21,13 @@ struct Bump {
 struct QrLayout {
     size_t flags, flag_bytes, beta, G, T, X, W, split;
     int64_t xcols, wcols, split_cap;
+    // tensor-core digit slices (split mode; caps 0 otherwise)
+    size_t tc_as, tc_bs, tc_ea, tc_fb, tc_as_cap, tc_bs_cap;
+    int64_t tc_sc_cap;
 };
+
+inline int split_slices(int P) { return (53 * P + 12 + 7) / 8; }
+inline int64_t round16(int64_t x) { return (x + 15) / 16 * 16; }
 struct BsLayout {
     size_t D, b;
 };
@@ -32,7 +38,8 @@ struct LsLayout {
     size_t total;
 };
 
-inline QrLayout qr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool want_q, int nextra) {
+inline QrLayout qr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool want_q, int nextra,
+                             bool keep_w = false, bool split = false) {
     QrLayout L;
     L.flag_bytes = align256((size_t)t * sizeof(unsigned int));
     L.flags = B.take(L.flag_bytes);
@@ -43,10 +50,28 @@ inline QrLayout qr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool w
     L.xcols = n + nextra;
     if (want_q && m > L.xcols) L.xcols = m;
     L.X = B.take(d * t * (size_t)L.xcols);
-    L.wcols = want_q ? n : t;
+    L.wcols = (want_q || keep_w) ? n : t;
     L.W = B.take(d * (size_t)m * (size_t)L.wcols);
     L.split_cap = 16 * (int64_t)t * t;   // split-K partial sums, md values per plane
     L.split = B.take(d * (size_t)L.split_cap);
+    L.tc_as = L.tc_bs = L.tc_ea = L.tc_fb = 0;
+    L.tc_as_cap = L.tc_bs_cap = 0;
+    L.tc_sc_cap = 0;
+    if (split) {
+        // A operands: W^T, Y^T (t x m) and Y, W (m x t); B operands: the trailing
+        // columns and right-hand sides, Q (m x m), X, T, Y (K <= m)
+        const int64_t S = split_slices(P), mp = round16(m), tp = round16(t);
+        int64_t bcols = n + nextra;
+        if (want_q && m > bcols) bcols = m;
+        if (t > bcols) bcols = t;
+        L.tc_as_cap = (size_t)S * (size_t)((t * mp > m * tp) ? t * mp : m * tp);
+        L.tc_bs_cap = (size_t)S * (size_t)(bcols * mp);
+        L.tc_sc_cap = (m > bcols ? m : bcols);
+        L.tc_as = B.take(2 * L.tc_as_cap);
+        L.tc_bs = B.take(2 * L.tc_bs_cap);
+        L.tc_ea = B.take(4 * (size_t)L.tc_sc_cap);
+        L.tc_fb = B.take(4 * (size_t)L.tc_sc_cap);
+    }
     return L;
 }
 
@@ -60,9 +85,9 @@ inline BsLayout bs_layout_at(Bump& B, int P, int64_t n, int t) {
 }
 
 inline QrLayout qr_layout(int P, int64_t m, int64_t n, int t, bool want_q, int nextra,
-                          size_t* total = nullptr) {
+                          size_t* total = nullptr, bool split = false) {
     Bump B;
-    QrLayout L = qr_layout_at(B, P, m, n, t, want_q, nextra);
+    QrLayout L = qr_layout_at(B, P, m, n, t, want_q, nextra, false, split);
     if (total) *total = B.off;
     return L;
 }
@@ -74,10 +99,41 @@ inline BsLayout bs_layout(int P, int64_t n, int t, size_t* total = nullptr) {
     return L;
 }
 
-inline LsLayout ls_layout(int P, int64_t m, int64_t n, int t) {
+// Least squares by double-double factorisation and refinement in P limbs:
+// the dd QR of A (every tile's W kept), dd back substitution, and the
+// vectors of the refinement loop.
+struct RefLayout {
+    QrLayout qr;
+    size_t A2, res, f, g, c, h, d, up, splitP;
+    int64_t splitP_cap;
+    BsLayout bs;
+    size_t total;
+};
+
+inline RefLayout ref_layout(int P, int64_t m, int64_t n, int t) {
+    Bump B;
+    RefLayout L;
+    L.qr = qr_layout_at(B, 2, m, n, t, false, 0, true);
+    const size_t d2 = 2 * sizeof(double), dP = (size_t)P * sizeof(double);
+    L.A2 = B.take(d2 * (size_t)m * (size_t)n);
+    L.res = B.take(dP * (size_t)m);
+    L.f = B.take(dP * (size_t)m);
+    L.g = B.take(dP * (size_t)n);
+    L.c = B.take(d2 * (size_t)m);
+    L.h = B.take(d2 * (size_t)n);
+    L.d = B.take(d2 * (size_t)n);
+    L.up = B.take(dP * (size_t)m);
+    L.splitP_cap = 16 * (m > n ? m : n);
+    L.splitP = B.take(dP * (size_t)L.splitP_cap);
+    L.bs = bs_layout_at(B, 2, n, t);
+    L.total = B.off;
+    return L;
+}
+
+inline LsLayout ls_layout(int P, int64_t m, int64_t n, int t, bool split = false) {
     Bump B;
     LsLayout L;
-    L.qr = qr_layout_at(B, P, m, n, t, false, 1);
+    L.qr = qr_layout_at(B, P, m, n, t, false, 1, false, split);
     L.Aw = B.take(sizeof(double) * (size_t)P * (size_t)m * (size_t)(n + 1));
     L.bs = bs_layout_at(B, P, n, t);
     L.total = B.off;

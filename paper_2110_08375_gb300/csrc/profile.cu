@@ -44,7 +44,8 @@ const char* kNames[ST_COUNT] = {"panel (beta, v; beta R^T v; update R)",
                                 "invert diagonal tiles",
                                 "multiply with inverses",
                                 "back substitution (right-hand side update)",
-                                "other (copies, identity, zeroing, vector ops)"};
+                                "other (copies, identity, zeroing, vector ops)",
+                                "refinement (residuals, Q^T r, corrections)"};
 
 }  // namespace
 

@@ -20,6 +20,7 @@ enum Stage {
     ST_MULINV,      // "multiply with inverses"
     ST_BSUPD,       // "back substitution" (right-hand side updates)
     ST_OTHER,       // copies, identity, zeroing, elementwise ops
+    ST_REFINE,      // refinement: residuals in P limbs, Q^T r and corrections
     ST_COUNT
 };
 

@@ -45,7 +45,7 @@ def test_every_declared_symbol_is_exported(L):
 def test_version_and_status_strings(L):
     assert L.mdls_version() >= 100
     import paper_2110_08375_gb300 as pkg
-    for code in range(-7, 1):
+    for code in range(-8, 1):
         s = pkg.status_string(code)
         assert s and s != "unknown status"
     assert pkg.status_string(-99) == "unknown status"
