@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-modes", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch", type=int, default=512)
     return ap.parse_args()
 
 
@@ -342,6 +344,8 @@ def run_gpu(args):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 ms = 0.0
+                mdls.mdls_profile_enable(True)
+                mdls.mdls_profile_read()
                 for _ in range(args.steps):
                     flush.zero_()
                     e0.record(stream)
@@ -349,15 +353,25 @@ def run_gpu(args):
                     e1.record(stream)
                     torch.cuda.synchronize()
                     ms += e0.elapsed_time(e1)
+                mstages = mdls.mdls_profile_read()
+                mdls.mdls_profile_enable(False)
                 ms /= args.steps
                 diff = (xm - plain_x[p]).sum(dim=0).abs().max().item()
                 scale = plain_x[p][0].abs().max().item()
                 res[PREC_NAMES[p]] = {"ms": ms, "speedup_vs_plain": (per_prec_ms[p] / args.steps) / ms,
                                       "table1_tflops": fl[p] / (ms / 1e3) / 1e12,
-                                      "rel_diff_vs_plain": diff / scale, "status": st}
+                                      "rel_diff_vs_plain": diff / scale, "status": st,
+                                      "stages_ms": {k2: round(v2[0] / args.steps, 3) for k2, v2 in mstages.items()
+                                                    if v2[0] > 0}}
                 del wsm
             modes[mname] = res
         out["modes"] = modes
+
+    # batched: the mixed workload (n ~ log-uniform [32, 512], m = n + U{0..n},
+    # half dd, half qd) solved by one graph launch, against a loop of single
+    # mdls_lstsq calls (default tile, one reused workspace) on the same stream
+    if not args.no_batched:
+        out["batched"] = run_batched(args, dev, stream, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(128, precs)
@@ -365,6 +379,66 @@ def run_gpu(args):
     if rank == 0:
         print(json.dumps(out), flush=True)
     barrier(world)
+
+
+def run_batched(args, dev, stream, flush):
+    import torch
+
+    import paper_2110_08375_gb300 as mdls
+    import synth
+    shapes = synth.batched_shapes(args.batch, seed=0)
+    probs = []
+    for i, (m, n, p) in enumerate(shapes):
+        A, b = synth.batched_problem(i, m, n, p, seed=0)
+        probs.append((torch.from_numpy(A).to(dev), torch.from_numpy(b).to(dev),
+                      torch.zeros((p, n), dtype=torch.float64, device=dev)))
+    t0 = time.perf_counter()
+    plan = mdls.mdls_batched_plan(probs, autotune=True)
+    plan_s = time.perf_counter() - t0
+    plan.launch(stream)
+    torch.cuda.synchronize()
+    status = plan.status()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    graph_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        plan.launch(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms += e0.elapsed_time(e1)
+    graph_ms /= args.steps
+    batched_x = [x.clone() for (_, _, x) in probs]
+    # loop of single solves
+    need = max(mdls.mdls_lstsq_workspace(p, m, n, 0) for (m, n, p) in shapes)
+    ws = mdls.workspace(need, dev)
+    def loop():
+        for (A, b_, x) in probs:
+            mdls.mdls_lstsq(A, b_, x, tile=0, ws=ws)
+    loop()
+    torch.cuda.synchronize()
+    loop_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        loop()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        loop_ms += e0.elapsed_time(e1)
+    loop_ms /= args.steps
+    worst = 0.0
+    for xb, (_, _, x) in zip(batched_x, probs):
+        d = (xb - x).sum(dim=0).abs().max().item() / max(x[0].abs().max().item(), 1e-300)
+        worst = max(worst, d)
+    tiles = plan.tiles()
+    res = {"problems": len(shapes), "solves_per_s": len(shapes) / (graph_ms / 1e3),
+           "loop_solves_per_s": len(shapes) / (loop_ms / 1e3), "speedup_vs_loop": loop_ms / graph_ms,
+           "graph_ms": graph_ms, "loop_ms": loop_ms, "plan_s_with_autotune": plan_s,
+           "max_rel_diff_batched_vs_loop": worst, "nonzero_status": sum(1 for s in status if s != 0),
+           "tiles_used": sorted(set(tiles))}
+    plan.destroy()
+    return res
 
 
 def main():

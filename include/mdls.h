@@ -187,6 +187,52 @@ int mdls_vec_op(int prec, int op, int64_t count, const double* a, int64_t psa, c
                 int64_t psb, double* c, int64_t psc, void* stream);
 
 /*
+ * Batched least squares: many independent problems of mixed shape and
+ * precision solved by one launch of a CUDA graph (row a9 of the hot path;
+ * the paper solves one system at a time).
+ *   mdls_problem describes one problem, exactly as the arguments of
+ *   mdls_lstsq (device pointers, limb-planar layout, A and b read only, x
+ *   written); tile 0 lets the autotuner choose.
+ *   mdls_batched_workspace(): bytes of caller workspace for the problems
+ *   (0 if one of them is invalid).
+ *   mdls_batched_plan(): checks the problems, picks each tile -- the caller's,
+ *   else the autotuner's choice for the (prec, m, n) size class: when
+ *   autotune != 0, the first problem of a class never seen before in this
+ *   process is solved with each candidate tile (8..128) on its own buffers
+ *   and timed, and the fastest tile serves the whole class; otherwise a fixed
+ *   rule -- then captures every problem's kernels into one CUDA graph
+ *   (parallel branches, largest problems first, each problem with its own
+ *   slice of ws and a single-block panel) and instantiates it.  Planning
+ *   synchronises the device and must not run inside a stream capture.
+ *   mdls_batched_launch(): one graph launch solving every problem on stream.
+ *   mdls_batched_status(): waits for stream, then copies each problem's
+ *   device status (MDLS_OK, MDLS_ERR_SINGULAR, ...) to status[count] (host).
+ *   mdls_batched_tiles(): the tile of each problem, to tiles[count] (host).
+ *   mdls_batched_destroy(): frees the plan (not the caller's buffers).
+ * The plan keeps pointers to the problems' buffers and to ws: they must stay
+ * valid and must not move while the plan is used.
+ */
+typedef struct {
+    int prec;     /* 2, 4 or 8 limbs */
+    int tile;     /* 1..256, or 0: autotuned */
+    int64_t m, n; /* m >= n >= 1 */
+    const double* A;
+    int64_t lda, psa;
+    const double* b;
+    int64_t psb;
+    double* x;
+    int64_t psx;
+} mdls_problem;
+
+size_t mdls_batched_workspace(const mdls_problem* probs, int count);
+int mdls_batched_plan(const mdls_problem* probs, int count, void* ws, size_t ws_bytes, int autotune,
+                      void** plan);
+int mdls_batched_launch(void* plan, void* stream);
+int mdls_batched_status(void* plan, int* status, void* stream);
+int mdls_batched_tiles(void* plan, int* tiles);
+void mdls_batched_destroy(void* plan);
+
+/*
  * mdls_read_status -- waits for `stream`, then copies the device status word
  * of the workspace `ws` (MDLS_OK, MDLS_ERR_SINGULAR or MDLS_ERR_TIMEOUT) to
  * *status.  Returns MDLS_OK or MDLS_ERR_CUDA.

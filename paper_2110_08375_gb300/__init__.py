@@ -37,6 +37,13 @@ OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "fma": 4, "sqrt": 5}
 _lib = None
 
 
+class Problem(C.Structure):
+    """mdls_problem of include/mdls.h."""
+    _fields_ = [("prec", C.c_int), ("tile", C.c_int), ("m", C.c_int64), ("n", C.c_int64),
+                ("A", C.c_void_p), ("lda", C.c_int64), ("psa", C.c_int64),
+                ("b", C.c_void_p), ("psb", C.c_int64), ("x", C.c_void_p), ("psx", C.c_int64)]
+
+
 class MdlsError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -70,6 +77,14 @@ def lib() -> C.CDLL:
     L.mdls_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
     L.mdls_stage_name.argtypes = [C.c_int]
     L.mdls_stage_name.restype = C.c_char_p
+    L.mdls_batched_workspace.argtypes = [C.POINTER(Problem), C.c_int]
+    L.mdls_batched_workspace.restype = sz
+    L.mdls_batched_plan.argtypes = [C.POINTER(Problem), C.c_int, vp, sz, C.c_int, C.POINTER(vp)]
+    L.mdls_batched_launch.argtypes = [vp, vp]
+    L.mdls_batched_status.argtypes = [vp, C.POINTER(C.c_int), vp]
+    L.mdls_batched_tiles.argtypes = [vp, C.POINTER(C.c_int)]
+    L.mdls_batched_destroy.argtypes = [vp]
+    L.mdls_batched_destroy.restype = None
     L.mdls_vec_op.argtypes = [C.c_int, C.c_int, i64, vp, i64, vp, i64, vp, i64, vp]
     _lib = L
     return L
@@ -227,3 +242,71 @@ def mdls_profile_read() -> dict:
 
 def mdls_stage_name(stage: int) -> str:
     return lib().mdls_stage_name(int(stage)).decode()
+
+
+
+class BatchedPlan:
+    """A plan of mdls_batched_plan: one graph launch solves every problem.
+
+    problems: list of (A, b, x) or (A, b, x, tile) tensors, A (p, n, ld),
+    b (p, m), x (p, n) on the GPU.  The plan keeps references to them and to
+    its workspace, which must not be freed while the plan lives.
+    """
+
+    def __init__(self, problems, autotune: bool = True):
+        torch = _torch()
+        arr = (Problem * len(problems))()
+        self._keep = []
+        for i, pr in enumerate(problems):
+            A, b, x = pr[:3]
+            tile = pr[3] if len(pr) > 3 else 0
+            for t, nd, nm in ((A, 3, "A"), (b, 2, "b"), (x, 2, "x")):
+                _check_md(t, nd, nm)
+            p, n, lda = A.shape
+            arr[i] = Problem(p, tile, lda, n, A.data_ptr(), A.stride(1), A.stride(0), b.data_ptr(),
+                             b.stride(0), x.data_ptr(), x.stride(0))
+            self._keep.append((A, b, x))
+        self.count = len(problems)
+        need = lib().mdls_batched_workspace(arr, self.count)
+        if need == 0:
+            raise MdlsError(MDLS_ERR_ARG, "mdls_batched_workspace")
+        self.ws = workspace(need, self._keep[0][0].device)
+        handle = C.c_void_p()
+        torch.cuda.synchronize()
+        rc = lib().mdls_batched_plan(arr, self.count, self.ws.data_ptr(), need, int(autotune), C.byref(handle))
+        if rc != MDLS_OK:
+            raise MdlsError(rc, "mdls_batched_plan")
+        self.handle = handle
+        self._arr = arr
+
+    def launch(self, stream=None):
+        rc = lib().mdls_batched_launch(self.handle, _stream(stream))
+        if rc != MDLS_OK:
+            raise MdlsError(rc, "mdls_batched_launch")
+
+    def status(self, stream=None):
+        out = (C.c_int * self.count)()
+        rc = lib().mdls_batched_status(self.handle, out, _stream(stream))
+        if rc != MDLS_OK:
+            raise MdlsError(rc, "mdls_batched_status")
+        return list(out)
+
+    def tiles(self):
+        out = (C.c_int * self.count)()
+        lib().mdls_batched_tiles(self.handle, out)
+        return list(out)
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib().mdls_batched_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def mdls_batched_plan(problems, autotune: bool = True) -> BatchedPlan:
+    return BatchedPlan(problems, autotune)

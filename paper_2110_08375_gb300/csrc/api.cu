@@ -12,7 +12,7 @@ namespace mdls {
     int bs_entry_p##P(int64_t, const double*, int64_t, int64_t, const double*, int64_t, double*,  \
                       int64_t, int, void*, cudaStream_t);                                          \
     int ls_entry_p##P(int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t,  \
-                      double*, int64_t, int, int, void*, cudaStream_t);                            \
+                      double*, int64_t, int, int, void*, cudaStream_t, bool);                      \
     int vec_entry_p##P(int, int64_t, const double*, int64_t, const double*, int64_t, double*,     \
                        int64_t, cudaStream_t);                                                     \
     int ls_refine_entry_p##P(int64_t, int64_t, const double*, int64_t, int64_t, const double*,    \
@@ -128,9 +128,9 @@ int mdls_lstsq(int prec, int64_t m, int64_t n, const double* A, int64_t lda, int
         return ls_refine_entry_p8(m, n, A, lda, psa, b, psb, x, psx, t, 6, ws, st);
     }
     switch (prec) {
-        case 2: return ls_entry_p2(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st);
-        case 4: return ls_entry_p4(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st);
-        default: return ls_entry_p8(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st);
+        case 2: return ls_entry_p2(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st, false);
+        case 4: return ls_entry_p4(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st, false);
+        default: return ls_entry_p8(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st, false);
     }
 }
 

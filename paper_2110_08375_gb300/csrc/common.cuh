@@ -34,12 +34,15 @@ DEV_INLINE void st_md(double* __restrict__ ptr, int64_t ps, int64_t off, const m
 
 // Operand views for the md GEMM.  get(i, k, l) returns limb l of element
 // (i, k) of the operand as the GEMM sees it.
+// kRowContig: consecutive i are consecutive in memory (column-major rows).
 struct ViewDense {      // X(i, k)
+    static constexpr bool kRowContig = true;
     const double* ptr;
     int64_t ld, ps;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const { return ptr[l * ps + k * ld + i]; }
 };
 struct ViewDenseT {     // X(k, i): the transpose
+    static constexpr bool kRowContig = false;
     const double* ptr;
     int64_t ld, ps;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const { return ptr[l * ps + i * ld + k]; }
@@ -47,6 +50,7 @@ struct ViewDenseT {     // X(k, i): the transpose
 // Unit lower trapezoid Y of Householder vectors stored below the diagonal:
 // Y(i, k) = 0 for i < k, 1 for i == k, stored value for i > k.
 struct ViewTrap {
+    static constexpr bool kRowContig = true;
     const double* ptr;  // points at the panel's (0, 0)
     int64_t ld, ps;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const {
@@ -55,6 +59,7 @@ struct ViewTrap {
     }
 };
 struct ViewTrapT {      // Y^T
+    static constexpr bool kRowContig = false;
     const double* ptr;
     int64_t ld, ps;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const {
@@ -64,6 +69,7 @@ struct ViewTrapT {      // Y^T
 };
 // Upper triangular operand (entries below the diagonal read as zero).
 struct ViewUpper {
+    static constexpr bool kRowContig = true;
     const double* ptr;
     int64_t ld, ps;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const {
@@ -78,12 +84,59 @@ struct ViewUpper {
 struct WsHeader {
     int status;            // first error seen on the device (0 = none)
     int pad0;
-    unsigned int pad1[2];
-    int bar_error;         // set by a bounded wait that gave up: later waits fail fast
-    int pad2[59];          // header is 256 bytes
+    unsigned int bar_count;  // grid barrier: arrivals of the current generation
+    unsigned int bar_gen;    // grid barrier: generation
+    int bar_error;           // set by a bounded wait that gave up: later waits fail fast
+    int pad2[59];            // header is 256 bytes
 };
 static_assert(sizeof(WsHeader) == 256, "workspace header must be 256 bytes");
 
 DEV_INLINE void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  Every
+// wait is bounded: after about kBarrierTimeoutCycles the waiting block raises
+// bar_error and MDLS_ERR_TIMEOUT and returns false; once bar_error is set all
+// later barriers return false at once, so every block leaves the kernel in
+// bounded time.  A single block needs no barrier.
+constexpr long long kBarrierTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ bool grid_barrier(WsHeader* h) {
+    __syncthreads();
+    if (gridDim.x == 1) return true;
+    __shared__ int ok_s;
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &h->bar_gen;
+        volatile int* verr = &h->bar_error;
+        int ok = (*verr == 0);
+        if (ok) {
+            const unsigned int g = *vgen;
+            __threadfence();
+            const unsigned int arrived = atomicAdd(&h->bar_count, 1u);
+            if (arrived == gridDim.x - 1) {
+                h->bar_count = 0;
+                __threadfence();
+                atomicAdd(&h->bar_gen, 1u);
+            } else {
+                const long long t0 = clock64();
+                while (*vgen == g) {
+                    if (*verr) { ok = 0; break; }
+                    if (clock64() - t0 > kBarrierTimeoutCycles) {
+                        atomicExch(&h->bar_error, 1);
+                        set_status(&h->status, MDLS_ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        ok_s = ok;
+    }
+    __syncthreads();
+    const int ok = ok_s;
+    __syncthreads();
+    return ok != 0;
+}
 
 }  // namespace mdls

@@ -80,6 +80,44 @@ int launch_split_gemm(int stage, cudaStream_t st, const TcBuf& tc, int64_t M, in
     return MDLS_OK;
 }
 
+// One md matrix-vector product (N = 1), split along K when the rows alone
+// would leave SMs idle.
+template <int P, class AV, class BV>
+int launch_gemv(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t K, AV a, BV b, Dense c,
+                bool neg, bool acc) {
+    StageScope sc(stage, st);
+    constexpr bool rows = AV::kRowContig;
+    const int64_t per_block = rows ? 128 : 4;  // rows per 128-thread block
+    const int64_t blocks = (M + per_block - 1) / per_block;
+    const int64_t target = 2 * (int64_t)sm_count();
+    int64_t S = 1;
+    if (blocks < target && K >= 64 && sb.ptr != nullptr) {
+        S = (target + blocks - 1) / blocks;
+        if (S > 16) S = 16;
+        if (S > K / 32) S = K / 32;
+        while (S > 1 && S * M > sb.cap) --S;
+    }
+    int64_t kchunk = K > 0 ? K : 1;
+    if (S > 1) {
+        kchunk = (K + S - 1) / S;
+        S = (K + kchunk - 1) / kchunk;
+    }
+    dim3 grid((unsigned)blocks, (unsigned)S);
+    Dense out = S > 1 ? Dense{sb.ptr, M, sb.cap} : c;
+    const int n_ = S > 1 ? 0 : (neg ? 1 : 0), a_ = S > 1 ? 0 : (acc ? 1 : 0);
+    if (rows)
+        gemv_rows_kernel<P, AV, BV><<<grid, 128, 0, st>>>(M, K, a, b, out, n_, a_, kchunk, M);
+    else
+        gemv_warps_kernel<P, AV, BV><<<grid, 128, 0, st>>>(M, K, a, b, out, n_, a_, kchunk, M);
+    MDLS_LAUNCH_CHECK();
+    if (S > 1) {
+        split_reduce_kernel<P><<<(unsigned)((M + 127) / 128), 128, 0, st>>>(M, 1, (int)S, sb.ptr, M, sb.cap, M,
+                                                                          c, neg ? 1 : 0, acc ? 1 : 0);
+        MDLS_LAUNCH_CHECK();
+    }
+    return MDLS_OK;
+}
+
 // Launches one md GEMM.  When the output grid alone would leave SMs idle,
 // the K range is split over grid.z (at most 16 ways, partials in `sb`) and a
 // reduction kernel adds the partials in a fixed order.
@@ -94,6 +132,7 @@ int launch_gemm(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t N, i
             M <= sb.tc->sc_cap && N <= sb.tc->sc_cap)
             return launch_split_gemm<P>(stage, st, *sb.tc, M, N, K, a, b, c, neg, acc);
     }
+    if (N == 1 && !upper_only) return launch_gemv<P>(stage, st, sb, M, K, a, b, c, neg, acc);
     StageScope sc(stage, st);
     const int64_t gx = (M + kGemmTile - 1) / kGemmTile, gy = (N + kGemmTile - 1) / kGemmTile;
     const int64_t tiles = upper_only ? (gx * (gx + 1)) / 2 : gx * gy;
@@ -130,17 +169,15 @@ int launch_gemm(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t N, i
     return MDLS_OK;
 }
 
-// largest panel width the cooperative launch can hold on this device
+// Largest panel width the column-per-block cooperative panel can hold.
 template <int P>
 int panel_capacity() {
     static int cap = -1;
     if (cap < 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_kernel<P, panel_threads<P>()>,
                                                       panel_threads<P>(), 0);
-        cap = sms * per;
+        cap = sm_count() * per;
     }
     return cap;
 }
@@ -153,15 +190,17 @@ int panel_capacity() {
 template <int P>
 int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa, double* Q,
            int64_t ldq, int64_t psq, int t, char* ws, const QrLayout& L, WsHeader* hdr,
-           bool zero_lower, cudaStream_t st, bool keep_w = false) {
+           bool zero_lower, cudaStream_t st, bool keep_w = false, bool single_block = false) {
     constexpr int NT = panel_threads<P>();
-    if (t > panel_capacity<P>()) return MDLS_ERR_UNSUPPORTED;
     double* beta = reinterpret_cast<double*>(ws + L.beta);
     double* G = reinterpret_cast<double*>(ws + L.G);
     double* T = reinterpret_cast<double*>(ws + L.T);
     double* X = reinterpret_cast<double*>(ws + L.X);
     double* Wb = reinterpret_cast<double*>(ws + L.W);
     unsigned int* flags = reinterpret_cast<unsigned int*>(ws + L.flags);
+    double* part = reinterpret_cast<double*>(ws + L.part);
+    double* wvec = reinterpret_cast<double*>(ws + L.wvec);
+    const int64_t part_ps = (int64_t)kMaxPanelBlocks * (t + 1);
     TcBuf tcb{};
     if (L.tc_as_cap > 0) {
         tcb = TcBuf{reinterpret_cast<__nv_bfloat16*>(ws + L.tc_as), reinterpret_cast<__nv_bfloat16*>(ws + L.tc_bs),
@@ -181,14 +220,23 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
         const int64_t j0 = k * t;
         const int w = (int)((n - j0) < t ? (n - j0) : t);
         const int64_t r = m - j0;
-        // 1. panel: Householder vectors, beta, R_kk
-        PanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, flags, (unsigned int)(k + 1), hdr};
-        void* args[] = {&pa};
+        // 1. panel: Householder vectors, beta, R_kk.  One block per column with
+        //    flags between them (cooperative launch); small problems of batched
+        //    solves use the single-block panel instead.
         {
             StageScope sc(ST_PANEL, st);
-            if (cudaLaunchCooperativeKernel((const void*)panel_kernel<P, NT>, dim3(w), dim3(NT), args,
-                                            0, st) != cudaSuccess)
-                return MDLS_ERR_CUDA;
+            if (single_block) {
+                RowPanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, part, part_ps, wvec, hdr};
+                panel_rows_kernel<P, NT><<<1, NT, 0, st>>>(pa);
+                MDLS_LAUNCH_CHECK();
+            } else {
+                if (w > panel_capacity<P>()) return MDLS_ERR_UNSUPPORTED;
+                PanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, flags, (unsigned int)(k + 1), hdr};
+                void* args[] = {&pa};
+                if (cudaLaunchCooperativeKernel((const void*)panel_kernel<P, NT>, dim3(w), dim3(NT), args, 0,
+                                                st) != cudaSuccess)
+                    return MDLS_ERR_CUDA;
+            }
         }
         const int64_t nc = n + nextra - (j0 + w);  // trailing columns incl. right-hand sides
         if (nc <= 0 && !want_q && !keep_w) continue;
@@ -401,7 +449,8 @@ int bs_entry(int64_t n, const double* R, int64_t ldr, int64_t psr, const double*
 
 template <int P>
 int ls_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa, const double* b,
-             int64_t psb, double* x, int64_t psx, int t, int mode, void* ws, cudaStream_t st) {
+             int64_t psb, double* x, int64_t psx, int t, int mode, void* ws, cudaStream_t st,
+             bool single_block = false) {
     LsLayout L = ls_layout(P, m, n, t, mode == MDLS_MODE_SPLIT);
     char* w = static_cast<char*>(ws);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(w);
@@ -416,7 +465,8 @@ int ls_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa, co
                             cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return MDLS_ERR_CUDA;
     }
-    int rc = qr_run<P>(m, n, 1, Aw, m, psw, nullptr, 0, 0, t, w, L.qr, hdr, false, st);
+    int rc = qr_run<P>(m, n, 1, Aw, m, psw, nullptr, 0, 0, t, w, L.qr, hdr, false, st, false,
+                       single_block);
     if (rc) return rc;
     return bs_run<P>(n, Aw, m, psw, Aw + n * m, psw, x, psx, t, w, L.bs, hdr, st);
 }
@@ -550,8 +600,8 @@ int ls_refine_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t 
     }                                                                                             \
     int ls_entry_p##P(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa,            \
                       const double* b, int64_t psb, double* x, int64_t psx, int t, int mode,      \
-                      void* ws, cudaStream_t st) {                                                \
-        return ls_entry<P>(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st);                  \
+                      void* ws, cudaStream_t st, bool single_block) {                             \
+        return ls_entry<P>(m, n, A, lda, psa, b, psb, x, psx, t, mode, ws, st, single_block);    \
     }                                                                                             \
     int ls_refine_entry_p##P(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa,     \
                              const double* b, int64_t psb, double* x, int64_t psx, int t,         \

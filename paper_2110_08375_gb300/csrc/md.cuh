@@ -309,25 +309,56 @@ MD_INLINE md<P> md_fma_d(const md<P>& c, double q, const md<P>& b) {
     return renorm<P>(s);
 }
 
+// Truncation / extension between precisions (no arithmetic).
+template <int Q, int P>
+MD_INLINE md<Q> md_take(const md<P>& x) {
+    md<Q> r;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) r.v[l] = l < P ? x.v[l] : 0.0;
+    return r;
+}
+
 // a / b by long division: quotient digit q_k = r_k / b_0 (one double
-// division), exact-ish remainder r_{k+1} = r_k - q_k b in md arithmetic,
-// P+1 digits, then the digits (each ~2^-52 below the previous) are
-// renormalised to P limbs.
+// division) and remainder r_{k+1} = r_k - q_k b.  The remainder after k
+// digits is ~2^(-52k) |a| and only its leading min(P, P+1-k) limbs matter
+// for a P-limb quotient, so later digits run in fewer limbs.  The P+1
+// digits (each ~2^-52 below the previous) are renormalised to P limbs.
+template <int P, int K, int Q>
+MD_INLINE void long_div(const md<Q>& r, const md<P>& b, double (&q)[P + 1]) {
+    q[K] = r.v[0] / b.v[0];
+    if constexpr (K < P) {
+        constexpr int Q2 = (P + 1 - (K + 1)) < P ? (P + 1 - (K + 1)) : P;
+        constexpr int QN = Q2 < 1 ? 1 : Q2;
+        const md<QN> rn = md_fma_d<QN>(md_take<QN>(r), -q[K], md_take<QN>(b));
+        long_div<P, K + 1, QN>(rn, b, q);
+    }
+}
+
 template <int P>
 MD_INLINE md<P> md_div(const md<P>& a, const md<P>& b) {
     double q[P + 1];
-    md<P> r = a;
-#pragma unroll
-    for (int k = 0; k <= P; ++k) {
-        q[k] = r.v[0] / b.v[0];
-        if (k < P) r = md_fma_d<P>(r, -q[k], b);
-    }
+    long_div<P, 0, P>(a, b, q);
     return renorm_n<P + 1, P>(q);
 }
 
-// sqrt(a) for a >= 0: x <- x + (a - x^2) / (2 x_0), each step gaining about
-// 53 bits, from the double square root of the leading limb.  Zero for a == 0,
-// NaN limbs for a < 0.
+// sqrt(a) for a >= 0: x <- x + (a - x^2) / (2 x_0) from the double square
+// root of the leading limb; each step gains ~53 bits, so step k works in
+// min(P, k+2) limbs (x has at most k+1 nonzero limbs before it).  Zero for
+// a == 0, NaN limbs for a < 0.
+template <int P, int IT>
+MD_INLINE void sqrt_steps(const md<P>& a, md<P>& x) {
+    if constexpr (IT < P) {
+        constexpr int Q = (IT + 2) < P ? (IT + 2) : P;
+        const md<Q> xq = md_take<Q>(x);
+        const md<Q> r = md_fms<Q>(md_take<Q>(a), xq, xq);
+        const double d = r.v[0] / dmul(2.0, x.v[0]);
+        const md<Q> xn = md_add<Q>(xq, md_from_double<Q>(d));
+#pragma unroll
+        for (int l = 0; l < P; ++l) x.v[l] = l < Q ? xn.v[l] : 0.0;
+        sqrt_steps<P, IT + 1>(a, x);
+    }
+}
+
 template <int P>
 MD_INLINE md<P> md_sqrt(const md<P>& a) {
     if (a.v[0] == 0.0) return md_zero<P>();
@@ -338,13 +369,7 @@ MD_INLINE md<P> md_sqrt(const md<P>& a) {
         return r;
     }
     md<P> x = md_from_double<P>(sqrt(a.v[0]));
-#pragma unroll
-    for (int it = 0; it < P; ++it) {
-        md<P> r = md_fms<P>(a, x, x);
-        double d = r.v[0] / dmul(2.0, x.v[0]);
-        md<P> dd = md_from_double<P>(d);
-        x = md_add<P>(x, dd);
-    }
+    sqrt_steps<P, 0>(a, x);
     return x;
 }
 

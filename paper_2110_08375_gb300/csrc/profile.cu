@@ -106,6 +106,27 @@ int mdls_profile_read(double* ms, int64_t* launches, int cap) {
     return rc == MDLS_OK ? ST_COUNT : rc;
 }
 
+}  // extern "C"
+
+namespace mdls {
+// Pauses event timing (launch counts continue) while a graph is captured,
+// so that no timing events are recorded into the graph; returns the old state.
+bool profiler_pause() {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    const bool old = p.timing;
+    p.timing = false;
+    return old;
+}
+void profiler_resume(bool on) {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.timing = on;
+}
+}  // namespace mdls
+
+extern "C" {
+
 const char* mdls_stage_name(int stage) {
     if (stage < 0 || stage >= ST_COUNT) return "unknown stage";
     return kNames[stage];

@@ -25,6 +25,8 @@ enum Stage {
 };
 
 void stage_begin(int stage, cudaStream_t st);
+bool profiler_pause();
+void profiler_resume(bool on);
 void stage_end(int stage, cudaStream_t st);
 
 struct StageScope {
