@@ -418,15 +418,12 @@ def run_batched(args, dev, stream, flush):
             mdls.mdls_lstsq(A, b_, x, tile=0, ws=ws)
     loop()
     torch.cuda.synchronize()
-    loop_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0.record(stream)
-        loop()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        loop_ms += e0.elapsed_time(e1)
-    loop_ms /= args.steps
+    flush.zero_()
+    e0.record(stream)
+    loop()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1)
     worst = 0.0
     for xb, (_, _, x) in zip(batched_x, probs):
         d = (xb - x).sum(dim=0).abs().max().item() / max(x[0].abs().max().item(), 1e-300)

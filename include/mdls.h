@@ -196,11 +196,11 @@ int mdls_vec_op(int prec, int op, int64_t count, const double* a, int64_t psa, c
  *   mdls_batched_workspace(): bytes of caller workspace for the problems
  *   (0 if one of them is invalid).
  *   mdls_batched_plan(): checks the problems, picks each tile -- the caller's,
- *   else the autotuner's choice for the (prec, m, n) size class: when
- *   autotune != 0, the first problem of a class never seen before in this
- *   process is solved with each candidate tile (8..128) on its own buffers
- *   and timed, and the fastest tile serves the whole class; otherwise a fixed
- *   rule -- then captures every problem's kernels into one CUDA graph
+ *   else the autotuner's choice for the size class (prec, n rounded down to
+ *   a power of two): when autotune != 0, the first problem of a class never
+ *   seen before in this process is solved with each candidate tile (8, 16,
+ *   32) on its own buffers and timed, and the fastest tile serves the whole
+ *   class; otherwise a fixed rule -- then captures every problem's kernels into one CUDA graph
  *   (parallel branches, largest problems first, each problem with its own
  *   slice of ws and a single-block panel) and instantiates it.  Planning
  *   synchronises the device and must not run inside a stream capture.

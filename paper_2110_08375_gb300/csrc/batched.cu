@@ -9,11 +9,11 @@
 // blocks of its own that the others keep off the SMs.  mdls_batched_launch()
 // replays the graph on a stream.
 //
-// Autotuner: for every (precision, m-bucket, n-bucket) not seen before, the
-// first problem of that class is solved with each candidate tile (8, 16, 32,
-// 64, 128 that fit) on the problem's own buffers, timed with CUDA events
-// (one warm-up, median of three), and the fastest tile is kept in a
-// process-wide table for every later problem of the class.
+// Autotuner: for every (precision, n-bucket) class not seen before (n
+// buckets are powers of two), the first problem of that class is solved with
+// each candidate tile (8, 16, 32 that fit) on the problem's own buffers,
+// timed with CUDA events after one warm-up, and the fastest tile is kept in
+// a process-wide table for every later problem of the class.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,7 +39,7 @@ using namespace mdls;
 
 namespace {
 
-const int kCandidates[] = {8, 16, 32, 64, 128};
+const int kCandidates[] = {8, 16, 32};
 constexpr int kBranches = 32;
 
 int solve_one(const mdls_problem& p, int tile, void* ws, cudaStream_t st) {
@@ -73,7 +73,7 @@ int bucket(int64_t v) {  // powers of two
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tune;  // (prec, m bucket, n bucket) -> tile
+std::map<std::tuple<int, int>, int> g_tune;  // (prec, n bucket) -> tile
 
 int heuristic_tile(const mdls_problem& p) {
     const int t = p.n <= 64 ? 16 : (p.n <= 256 ? 32 : 64);
@@ -98,19 +98,14 @@ int autotune(const mdls_problem& p, void* ws, int* rc) {
         if (t == last) continue;
         last = t;
         if (solve_one(p, t, ws, st) != MDLS_OK) continue;
-        float times[3];
-        bool ok = true;
-        for (int r = 0; r < 3 && ok; ++r) {
-            cudaEventRecord(e0, st);
-            ok = solve_one(p, t, ws, st) == MDLS_OK;
-            cudaEventRecord(e1, st);
-            ok = ok && cudaEventSynchronize(e1) == cudaSuccess &&
-                 cudaEventElapsedTime(&times[r], e0, e1) == cudaSuccess;
-        }
+        float ms = 0.f;
+        cudaEventRecord(e0, st);
+        bool ok = solve_one(p, t, ws, st) == MDLS_OK;
+        cudaEventRecord(e1, st);
+        ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
         if (!ok) continue;
-        std::sort(times, times + 3);
-        if (times[1] < best_ms) {
-            best_ms = times[1];
+        if (ms < best_ms) {
+            best_ms = ms;
             best_t = t;
         }
     }
@@ -170,7 +165,7 @@ int mdls_batched_plan(const mdls_problem* probs, int count, void* ws, size_t ws_
         if (p.tile > 0) {
             t = norm_tile(p.tile, p.n);
         } else {
-            const auto key = std::make_tuple(p.prec, bucket(p.m), bucket(p.n));
+            const auto key = std::make_tuple(p.prec, bucket(p.n));
             std::lock_guard<std::mutex> g(g_tune_mu);
             auto it = g_tune.find(key);
             if (it != g_tune.end()) {

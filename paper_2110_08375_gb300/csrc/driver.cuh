@@ -198,6 +198,7 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
     double* X = reinterpret_cast<double*>(ws + L.X);
     double* Wb = reinterpret_cast<double*>(ws + L.W);
     unsigned int* flags = reinterpret_cast<unsigned int*>(ws + L.flags);
+    double* pub = reinterpret_cast<double*>(ws + L.pub);
     double* part = reinterpret_cast<double*>(ws + L.part);
     double* wvec = reinterpret_cast<double*>(ws + L.wvec);
     const int64_t part_ps = (int64_t)kMaxPanelBlocks * (t + 1);
@@ -231,11 +232,16 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
                 MDLS_LAUNCH_CHECK();
             } else {
                 if (w > panel_capacity<P>()) return MDLS_ERR_UNSUPPORTED;
-                PanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, flags, (unsigned int)(k + 1), hdr};
+                PanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, pub, flags, (unsigned int)(k + 1), hdr};
                 void* args[] = {&pa};
                 if (cudaLaunchCooperativeKernel((const void*)panel_kernel<P, NT>, dim3(w), dim3(NT), args, 0,
                                                 st) != cudaSuccess)
                     return MDLS_ERR_CUDA;
+                if (r > 1) {
+                    dim3 g((unsigned)((r - 1 + 127) / 128), (unsigned)w);
+                    panel_scale_kernel<P><<<g, 128, 0, st>>>(A, lda, psa, j0, r, w, pub, 3 * (int64_t)t);
+                    MDLS_LAUNCH_CHECK();
+                }
             }
         }
         const int64_t nc = n + nextra - (j0 + w);  // trailing columns incl. right-hand sides

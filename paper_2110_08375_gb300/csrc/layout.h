@@ -21,7 +21,7 @@ struct Bump {
 constexpr int kMaxPanelBlocks = 512;
 
 struct QrLayout {
-    size_t flags, flag_bytes, beta, G, T, X, W, split, part, wvec;
+    size_t flags, flag_bytes, beta, pub, G, T, X, W, split, part, wvec;
     int64_t xcols, wcols, split_cap;
     // tensor-core digit slices (split mode; caps 0 otherwise)
     size_t tc_as, tc_bs, tc_ea, tc_fb, tc_as_cap, tc_bs_cap;
@@ -49,6 +49,7 @@ inline QrLayout qr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool w
     L.part = B.take(d * (size_t)kMaxPanelBlocks * (size_t)(t + 1));  // panel partial sums
     L.wvec = B.take(d * (size_t)t);
     L.beta = B.take(d * t);
+    L.pub = B.take(3 * d * t);  // panel: v0, beta', 1/v0 per column
     L.G = B.take(d * t * t);
     L.T = B.take(d * t * t);
     L.xcols = n + nextra;
