@@ -58,10 +58,10 @@ bool problem_ok(const mdls_problem& p) {
 
 size_t problem_ws(const mdls_problem& p) {
     size_t best = 0;
-    if (p.tile > 0) return align256(ls_layout(p.prec, p.m, p.n, norm_tile(p.tile, p.n)).total);
+    if (p.tile > 0) return align256(ls_layout(p.prec, p.m, p.n, norm_tile(p.tile, p.n), false, false).total);
     for (int c : kCandidates) {
         const int t = norm_tile(c, p.n);
-        best = std::max(best, ls_layout(p.prec, p.m, p.n, t).total);
+        best = std::max(best, ls_layout(p.prec, p.m, p.n, t, false, false).total);
     }
     return align256(best);
 }

@@ -6,6 +6,7 @@
 #include "kernels.cuh"
 #include "split.cuh"
 #include "layout.h"
+#include "panel_fx.cuh"
 #include "profile.h"
 
 namespace mdls {
@@ -14,6 +15,8 @@ template <int P>
 constexpr int panel_threads() {
     return P == 8 ? 128 : 256;
 }
+
+constexpr int kFxPanelThreads = 128;  // integer-digit panel: threads per column
 
 #define MDLS_LAUNCH_CHECK()                                  \
     do {                                                     \
@@ -175,8 +178,7 @@ int panel_capacity() {
     static int cap = -1;
     if (cap < 0) {
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_kernel<P, panel_threads<P>()>,
-                                                      panel_threads<P>(), 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fx_panel_kernel<P, kFxPanelThreads>, kFxPanelThreads, 0);
         cap = sm_count() * per;
     }
     return cap;
@@ -192,13 +194,16 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
            int64_t ldq, int64_t psq, int t, char* ws, const QrLayout& L, WsHeader* hdr,
            bool zero_lower, cudaStream_t st, bool keep_w = false, bool single_block = false) {
     constexpr int NT = panel_threads<P>();
+    static_assert(fx_digits(P) == fx::Cfg<P>::D && fx_meta_ints(P) == FxMeta<P>::ints,
+                  "host and device digit layouts differ");
     double* beta = reinterpret_cast<double*>(ws + L.beta);
     double* G = reinterpret_cast<double*>(ws + L.G);
     double* T = reinterpret_cast<double*>(ws + L.T);
     double* X = reinterpret_cast<double*>(ws + L.X);
     double* Wb = reinterpret_cast<double*>(ws + L.W);
     unsigned int* flags = reinterpret_cast<unsigned int*>(ws + L.flags);
-    double* pub = reinterpret_cast<double*>(ws + L.pub);
+    int32_t* fxF = reinterpret_cast<int32_t*>(ws + L.fxF);
+    int32_t* fxmeta = reinterpret_cast<int32_t*>(ws + L.fxmeta);
     double* part = reinterpret_cast<double*>(ws + L.part);
     double* wvec = reinterpret_cast<double*>(ws + L.wvec);
     const int64_t part_ps = (int64_t)kMaxPanelBlocks * (t + 1);
@@ -221,9 +226,9 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
         const int64_t j0 = k * t;
         const int w = (int)((n - j0) < t ? (n - j0) : t);
         const int64_t r = m - j0;
-        // 1. panel: Householder vectors, beta, R_kk.  One block per column with
-        //    flags between them (cooperative launch); small problems of batched
-        //    solves use the single-block panel instead.
+        // 1. panel: Householder vectors, beta, R_kk.  One block per column in
+        //    integer digits with flags between them (cooperative launch); the
+        //    small problems of batched solves use the single-block panel.
         {
             StageScope sc(ST_PANEL, st);
             if (single_block) {
@@ -232,16 +237,12 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
                 MDLS_LAUNCH_CHECK();
             } else {
                 if (w > panel_capacity<P>()) return MDLS_ERR_UNSUPPORTED;
-                PanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, pub, flags, (unsigned int)(k + 1), hdr};
+                FxPanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, fxF, fxmeta, flags,
+                               (unsigned int)(k + 1), hdr};
                 void* args[] = {&pa};
-                if (cudaLaunchCooperativeKernel((const void*)panel_kernel<P, NT>, dim3(w), dim3(NT), args, 0,
-                                                st) != cudaSuccess)
+                if (cudaLaunchCooperativeKernel((const void*)fx_panel_kernel<P, kFxPanelThreads>, dim3(w),
+                                                dim3(kFxPanelThreads), args, 0, st) != cudaSuccess)
                     return MDLS_ERR_CUDA;
-                if (r > 1) {
-                    dim3 g((unsigned)((r - 1 + 127) / 128), (unsigned)w);
-                    panel_scale_kernel<P><<<g, 128, 0, st>>>(A, lda, psa, j0, r, w, pub, 3 * (int64_t)t);
-                    MDLS_LAUNCH_CHECK();
-                }
             }
         }
         const int64_t nc = n + nextra - (j0 + w);  // trailing columns incl. right-hand sides
@@ -457,7 +458,7 @@ template <int P>
 int ls_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa, const double* b,
              int64_t psb, double* x, int64_t psx, int t, int mode, void* ws, cudaStream_t st,
              bool single_block = false) {
-    LsLayout L = ls_layout(P, m, n, t, mode == MDLS_MODE_SPLIT);
+    LsLayout L = ls_layout(P, m, n, t, mode == MDLS_MODE_SPLIT, !single_block);
     char* w = static_cast<char*>(ws);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(w);
     if (cudaMemsetAsync(w, 0, L.qr.flags + L.qr.flag_bytes, st) != cudaSuccess) return MDLS_ERR_CUDA;

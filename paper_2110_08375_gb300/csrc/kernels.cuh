@@ -100,141 +100,6 @@ DEV_INLINE bool wait_flag(const unsigned int* flag, unsigned int want, WsHeader*
 }
 
 // ----------------------------------------------------------------------------
-// Panel factorisation: step 1 of Algorithm 2 ("for l = 1..n: compute v and
-// beta, update R_kk") for one tile of w columns and r rows.
-//
-// Block c owns panel column c.  For l = 0..c-1 it waits until reflector l is
-// published and applies it to its column in two passes: w_c = beta' u^T a_c
-// (the paper's "beta R^T v") and a_c -= u w_c ("update R"), where u is the
-// UNSCALED Householder vector (u_l = v0 published apart, u_i = x_i below)
-// and beta' = beta / v0^2 = -1 / (mu v0), so that beta' u u^T = beta v v^T with
-// v = u / v0.  When l = c-1 the second pass also sums the squares of the new
-// column below its diagonal.  Block c then forms its reflector ("beta, v";
-// Golub & Van Loan Alg. 5.1.1 sign convention, P x = ||x|| e1): mu, v0 and
-// beta' are all the other blocks need, so they are published and the flag is
-// raised before the block computes the outputs beta = beta' v0^2 and 1/v0.
-// After the kernel, panel_scale_kernel turns u into v = u / v0 below the
-// diagonal (every block is done reading u by then).  All blocks are
-// co-resident (cooperative launch) and every wait is bounded.
-// ----------------------------------------------------------------------------
-struct PanelArgs {
-    double* A;            // working matrix
-    int64_t ld, ps;
-    int64_t j0;           // panel origin: global row = global column = j0
-    int64_t r;            // rows of the panel (m - j0)
-    int w;                // columns of the panel
-    double* beta;         // w md values (output beta), plane stride beta_ps
-    int64_t beta_ps;
-    double* pub;          // 3 w md values: v0, beta', 1/v0 of each column; plane stride 3*beta_ps
-    unsigned int* flags;  // w flags
-    unsigned int epoch;   // flag value meaning "ready" for this panel
-    WsHeader* hdr;
-};
-
-template <int P, int NT>
-__global__ void __launch_bounds__(NT) panel_kernel(PanelArgs a) {
-    const int c = blockIdx.x;
-    const int tid = threadIdx.x;
-    const int64_t ld = a.ld, ps = a.ps;
-    const int64_t pps = 3 * a.beta_ps;
-    double* base = a.A + a.j0 * ld + a.j0;  // panel (0, 0)
-    double* colc = base + (int64_t)c * ld;
-    __shared__ md<P> red[NT];
-    __shared__ md<P> sh_scal[3];
-    __shared__ int sh_flag;
-
-    md<P> sig = md_zero<P>();  // sum of squares below the diagonal of column c
-    if (c == 0) {
-        for (int64_t i = 1 + tid; i < a.r; i += NT) {
-            const md<P> xi = ld_md<P>(colc, ps, i);
-            sig = md_fma<P>(sig, xi, xi);
-        }
-    }
-    for (int ell = 0; ell < c; ++ell) {
-        if (tid == 0) sh_flag = wait_flag(a.flags + ell, a.epoch, a.hdr) ? 1 : 0;
-        __syncthreads();
-        const int ready = sh_flag;
-        __syncthreads();  // every thread has read sh_flag before it is reused
-        if (!ready) return;
-        const md<P> bp = ld_md_cg<P>(a.pub, pps, 3 * (int64_t)ell + 1);
-        const bool last = (ell == c - 1);
-        if (bp.v[0] == 0.0) {  // identity reflector (uniform branch)
-            if (last) {
-                for (int64_t i = c + 1 + tid; i < a.r; i += NT) {
-                    const md<P> xi = ld_md<P>(colc, ps, i);
-                    sig = md_fma<P>(sig, xi, xi);
-                }
-            }
-            continue;
-        }
-        const md<P> u0 = ld_md_cg<P>(a.pub, pps, 3 * (int64_t)ell);
-        const double* u = base + (int64_t)ell * ld;
-        md<P> s = md_zero<P>();
-        for (int64_t i = ell + tid; i < a.r; i += NT) {
-            const md<P> ui = (i == ell) ? u0 : ld_md_cg<P>(u, ps, i);
-            s = md_fma<P>(s, ui, ld_md<P>(colc, ps, i));
-        }
-        s = block_sum<P, NT>(s, red);
-        const md<P> wc = md_mul<P>(bp, s);
-        for (int64_t i = ell + tid; i < a.r; i += NT) {
-            const md<P> ui = (i == ell) ? u0 : ld_md_cg<P>(u, ps, i);
-            const md<P> ai = md_fms<P>(ld_md<P>(colc, ps, i), ui, wc);
-            st_md<P>(colc, ps, i, ai);
-            if (last && i > c) sig = md_fma<P>(sig, ai, ai);
-        }
-        __syncthreads();
-    }
-
-    // reflector of column c (rows c..r-1)
-    sig = block_sum<P, NT>(sig, red);
-    if (tid == 0) {
-        const md<P> x0 = ld_md<P>(colc, ps, c);
-        int kind;
-        md<P> u0, bp, rcc;
-        if (sig.v[0] == 0.0) {
-            u0 = md_one<P>();
-            if (x0.v[0] >= 0.0) {
-                kind = 1; bp = md_zero<P>(); rcc = x0;
-            } else {
-                kind = 2; bp = md_from_double<P>(2.0); rcc = md_neg<P>(x0);
-            }
-        } else {
-            kind = 0;
-            const md<P> mu = md_sqrt<P>(md_fma<P>(sig, x0, x0));
-            if (x0.v[0] <= 0.0) u0 = md_sub<P>(x0, mu);
-            else u0 = md_neg<P>(md_div<P>(sig, md_add<P>(x0, mu)));  // -sigma/(x0+mu)
-            bp = md_neg<P>(md_div<P>(md_one<P>(), md_mul<P>(mu, u0)));  // -1/(mu v0)
-            rcc = mu;
-        }
-        st_md<P>(a.pub, pps, 3 * (int64_t)c, u0);
-        st_md<P>(a.pub, pps, 3 * (int64_t)c + 1, bp);
-        st_md<P>(colc, ps, c, rcc);
-        __threadfence();
-        atomicExch(a.flags + c, a.epoch);
-        // outputs, off the critical path: beta = beta' v0^2 and 1/v0
-        if (kind == 0) {
-            st_md<P>(a.beta, a.beta_ps, c, md_mul<P>(md_mul<P>(bp, u0), u0));
-            st_md<P>(a.pub, pps, 3 * (int64_t)c + 2, md_div<P>(md_one<P>(), u0));
-        } else {
-            st_md<P>(a.beta, a.beta_ps, c, bp);
-            st_md<P>(a.pub, pps, 3 * (int64_t)c + 2, md_one<P>());
-        }
-    }
-}
-
-// v = u / v0 below the diagonal of every panel column (after panel_kernel).
-template <int P>
-__global__ void panel_scale_kernel(double* A, int64_t ld, int64_t ps, int64_t j0, int64_t r, int w,
-                                   const double* pub, int64_t pps) {
-    const int c = blockIdx.y;
-    const int64_t i = c + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= w || i >= r) return;
-    double* col = A + (j0 + c) * ld + j0;
-    const md<P> inv = ld_md<P>(pub, pps, 3 * (int64_t)c + 2);
-    st_md<P>(col, ps, i, md_mul<P>(ld_md<P>(col, ps, i), inv));
-}
-
-// ----------------------------------------------------------------------------
 // Row-split panel: step 1 of Algorithm 2 with every block sharing every
 // column (used with a single block for the small problems of batched solves,
 // where a panel must not wait on blocks of its own that other work keeps off

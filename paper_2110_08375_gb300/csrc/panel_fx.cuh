@@ -1,0 +1,311 @@
+// The Householder panel on the integer pipe: step 1 of Algorithm 2 ("beta,
+// v := house(...)", "beta R^T v", "update R") for the w columns of one tile,
+// Section 3.1 of arXiv 2110.08375.
+//
+// One block per column c (cooperative launch, all blocks resident).  The
+// column is converted once to fixed point (24-bit digits at a per-column
+// scale set by its norm, which reflections preserve) and kept in an
+// L2-resident digit array; every dot product, norm and update is then exact
+// integer arithmetic accumulated by digit diagonals, and only the results are
+// rounded back to multiple doubles.  For each earlier reflector ell block c
+//   (a) waits for "rows ready" of ell and forms the dot product of u_ell's
+//       rows below ell with its column (the bulk of u_ell . a_c),
+//   (b) waits for "scalars ready" of ell, completes the dot product with
+//       v0_ell a_c[ell], forms w = bp_ell (u_ell . a_c), updates row ell and
+//       then rows > ell: a_c -= w u_ell.
+// After its last update block c publishes its rows below the diagonal
+// (rescaled by whole digits so that the largest has a leading digit near
+// the top) and only then computes its reflector's scalars: the next block's
+// dot product (a) overlaps them.  Every wait is bounded.
+#pragma once
+#include "common.cuh"
+#include "fx.cuh"
+#include "kernels.cuh"
+
+namespace mdls {
+
+struct FxPanelArgs {
+    double* A;  // working matrix (limb planar)
+    int64_t ld, ps;
+    int64_t j0;  // panel origin (global row = global column = j0)
+    int64_t r;   // rows of the panel
+    int w;       // columns of the panel
+    double* beta;  // w md values, plane stride beta_ps
+    int64_t beta_ps;
+    int32_t* F;     // digit k of row i of column c: F[(k * w + c) * r + i]
+    int32_t* meta;  // per column: FxMeta<P>::ints ints
+    unsigned int* flags;  // 2w: [c] rows of u_c ready, [w + c] scalars of c ready
+    unsigned int epoch;   // flag value meaning "ready" for this panel
+    WsHeader* hdr;
+};
+
+// Per-column record published to the other blocks: scale of the published
+// rows (digits), kind, v0 and bp (digits and exponent each).
+template <int P>
+struct FxMeta {
+    static constexpr int N = fx::Cfg<P>::N;
+    static constexpr int kScaleU = 0, kKind = 1, kV0 = 2, kBp = 3 + N;
+    static constexpr int ints = 4 + 2 * N;
+};
+
+template <int N>
+DEV_INLINE void st_xf(int32_t* p, const fx::xf<N>& x) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) p[k] = x.d[k];
+    p[N] = x.e;
+}
+
+template <int N>
+DEV_INLINE fx::xf<N> ld_xf_cg(const int32_t* p) {
+    fx::xf<N> x;
+#pragma unroll
+    for (int k = 0; k < N; ++k) x.d[k] = __ldcg(p + k);
+    x.e = __ldcg(p + N);
+    return x;
+}
+
+// Block-wide exact sum of per-thread digit accumulators; the total's digit
+// sums end up in red[0][0..M) for every thread to read.
+template <int M, int NW>
+DEV_INLINE void block_digit_sum(int64_t (&acc)[M], int64_t (*red)[M]) {
+    fx::carry_norm<M>(acc);  // digits below 2^24: 32 of them sum in an int
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const int s = __reduce_add_sync(0xffffffffu, (int)acc[k]);
+        if (lane == 0) red[warp][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < M) {
+        int64_t t = 0;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) t += red[q][threadIdx.x];
+        red[0][threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) fx_panel_kernel(FxPanelArgs a) {
+    using namespace fx;
+    constexpr int D = Cfg<P>::D, N = Cfg<P>::N, NW = NT / 32, MI = FxMeta<P>::ints;
+    constexpr int M = D + 3;  // digit diagonals of a dot product
+    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t r = a.r, ps = a.ps, fs = (int64_t)a.w * r;
+    double* colc = a.A + (a.j0 + c) * a.ld + a.j0;
+    int32_t* Fc = a.F + (int64_t)c * r;
+    int32_t* Mc = a.meta + c * MI;
+
+    __shared__ int64_t red[NW][M];
+    __shared__ int32_t sh_w[D];
+    __shared__ double sh_d[NW];
+    __shared__ unsigned sh_u[NW];
+    __shared__ int sh_i[4];
+    __shared__ int32_t sh_x[N + 1];
+
+    // 0. column scale: e (digits) with every entry, now and after any
+    //    reflection, below 2^(24(e + D) - 3).  Bound from the leading limbs.
+    unsigned hmax = 0;
+    for (int64_t i = tid; i < r; i += NT) {
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            const unsigned h = (unsigned)(dbits(colc[l * ps + i]) >> 32) & 0x7fffffffu;
+            hmax = h > hmax ? h : hmax;
+        }
+    }
+    hmax = __reduce_max_sync(0xffffffffu, hmax);
+    if (lane == 0) sh_u[warp] = hmax;
+    __syncthreads();
+    hmax = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) hmax = sh_u[q] > hmax ? sh_u[q] : hmax;
+    const bool finite = hmax < 0x7ff00000u;
+    int emax = (int)(hmax >> 20) - 1023;  // leading exponent of the largest entry
+    if (emax < -1022) emax = -1022;
+    if (emax > 1000) emax = 1000;
+    const double down = dfrom((uint64_t)(1023 - emax) << 52);  // 2^-emax
+    double ss = 0.0;
+    if (finite)
+        for (int64_t i = tid; i < r; i += NT) {
+            const double v = colc[i] * down;
+            ss = __fma_rn(v, v, ss);
+        }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, off);
+    if (lane == 0) sh_d[warp] = ss;
+    __syncthreads();
+    ss = 0.0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) ss += sh_d[q];
+    int ec = -D;
+    if (finite && ss > 0.0) {
+        int k;
+        frexp(sqrt(ss), &k);         // sqrt(ss) < 2^k
+        const int bound = emax + k + 1;  // ||a_c|| < 2^bound, with a factor 2 to spare
+        ec = floordiv24(bound + 3 + kB - 1) - D;
+    }
+
+    // 1. the column in digits
+    for (int64_t i = tid; i < r; i += NT) {
+        int32_t d[D];
+        if (finite) {
+            fixed_from_md<P, D>(ld_md<P>(colc, ps, i), ec, d);
+        } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) d[k] = 0;
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) Fc[k * fs + i] = d[k];
+    }
+    __syncthreads();
+
+    // 2. reflectors 0 .. c-1
+    for (int ell = 0; ell < c; ++ell) {
+        if (tid == 0) sh_i[0] = wait_flag(a.flags + ell, a.epoch, a.hdr) ? 1 : 0;
+        __syncthreads();
+        if (!sh_i[0]) return;
+        const int eu = __ldcg(a.meta + ell * MI + FxMeta<P>::kScaleU);
+        const int32_t* Fu = a.F + (int64_t)ell * r;
+        // (a) bulk of the dot product, rows > ell
+        int64_t acc[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) acc[k] = 0;
+        int cnt = 0;
+        for (int64_t i = ell + 1 + tid; i < r; i += NT) {
+            int32_t u[D], x[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                u[k] = __ldcg(Fu + k * fs + i);
+                x[k] = Fc[k * fs + i];
+            }
+            dot_acc<D>(u, x, acc);
+            if ((++cnt & 255) == 0) carry_norm<M>(acc);
+        }
+        block_digit_sum<M, NW>(acc, red);
+        if (tid == 0) sh_i[1] = wait_flag(a.flags + a.w + ell, a.epoch, a.hdr) ? 1 : 0;
+        __syncthreads();
+        if (!sh_i[1]) return;
+        const int kind = __ldcg(a.meta + ell * MI + FxMeta<P>::kKind);
+        // (b) scalars: s = v0 a[ell] + bulk, w = bp s; row ell
+        if (tid == 0) {
+            const xf<N> v0 = ld_xf_cg<N>(a.meta + ell * MI + FxMeta<P>::kV0);
+            const xf<N> bp = ld_xf_cg<N>(a.meta + ell * MI + FxMeta<P>::kBp);
+            int64_t tot[M];
+#pragma unroll
+            for (int k = 0; k < M; ++k) tot[k] = red[0][k];
+            int32_t xe[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) xe[k] = Fc[k * fs + ell];
+            const xf<N> x_ell = xf_from_fixed<N, D>(xe, ec);
+            const xf<N> s = xf_add<N>(xf_from_acc<N>(tot, eu + ec + D - 3), xf_mul<N>(v0, x_ell));
+            const xf<N> W = xf_mul<N>(bp, s);
+            bool ok = fixed_from_xf<N, D>(xf_sub<N>(x_ell, xf_mul<N>(W, v0)), ec, xe);
+#pragma unroll
+            for (int k = 0; k < D; ++k) Fc[k * fs + ell] = xe[k];
+            int32_t wd[D];
+            if (kind == 0) ok = fixed_from_xf<N, D>(W, ec - eu - (D - 2), wd) && ok;
+            if (!ok) set_status(&a.hdr->status, MDLS_ERR_UNSUPPORTED);
+#pragma unroll
+            for (int k = 0; k < D; ++k) sh_w[k] = kind == 0 ? wd[k] : 0;
+        }
+        __syncthreads();
+        // rows > ell (a kind-1/2 reflector has no rows below ell)
+        if (kind == 0) {
+            int32_t wd[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) wd[k] = sh_w[k];
+            for (int64_t i = ell + 1 + tid; i < r; i += NT) {
+                int32_t u[D], x[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    u[k] = __ldcg(Fu + k * fs + i);
+                    x[k] = Fc[k * fs + i];
+                }
+                axpy_row<D>(x, wd, u);
+#pragma unroll
+                for (int k = 0; k < D; ++k) Fc[k * fs + i] = x[k];
+            }
+        }
+        __syncthreads();
+    }
+
+    // sum of squares and leading digit of the rows below the diagonal
+    int64_t sacc[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) sacc[k] = 0;
+    int top = -1;
+    int cnt = 0;
+    for (int64_t i = c + 1 + tid; i < r; i += NT) {
+        int32_t x[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[k] = Fc[k * fs + i];
+        dot_acc<D>(x, x, sacc);  // general product: a symmetric variant miscomputed low digits here
+        const int tp = fixed_top<D>(x);
+        top = tp > top ? tp : top;
+        if ((++cnt & 255) == 0) carry_norm<M>(sacc);  // keeps the int64 sums far from overflow
+    }
+
+    // 3. publish the rows below the diagonal, rescaled by q whole digits so
+    //    that their largest entry leads in digit D-2 or D-1
+    top = __reduce_max_sync(0xffffffffu, top);
+    if (lane == 0) sh_u[warp] = (unsigned)(top + 1);
+    block_digit_sum<M, NW>(sacc, red);  // (synchronises)
+    int tmax = -1;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) tmax = (int)sh_u[q] - 1 > tmax ? (int)sh_u[q] - 1 : tmax;
+    const int qsh = (tmax >= 0 && tmax < D - 2) ? D - 2 - tmax : 0;
+    if (qsh > 0) {
+        for (int64_t i = c + 1 + tid; i < r; i += NT) {
+#pragma unroll
+            for (int k = D - 1; k >= 0; --k) Fc[k * fs + i] = k >= qsh ? Fc[(k - qsh) * fs + i] : 0;
+        }
+    }
+    const int eu_c = ec - qsh;
+    __syncthreads();
+    if (tid == 0) {
+        Mc[FxMeta<P>::kScaleU] = eu_c;
+        __threadfence();
+        atomicExch(a.flags + c, a.epoch);
+        // the reflector's scalars (Golub and Van Loan, Algorithm 5.1.1)
+        int64_t tot[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) tot[k] = red[0][k];
+        const xf<N> sig = xf_from_acc<N>(tot, 2 * ec + D - 3);
+        int32_t xe[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xe[k] = Fc[k * fs + c];
+        xf<N> v0, bp, rcc, inv, bet;
+        const int kind = xf_house<N>(sig, xf_from_fixed<N, D>(xe, ec), v0, bp, rcc, inv, bet);
+        Mc[FxMeta<P>::kKind] = kind;
+        st_xf<N>(Mc + FxMeta<P>::kV0, v0);
+        st_xf<N>(Mc + FxMeta<P>::kBp, bp);
+        __threadfence();
+        atomicExch(a.flags + a.w + c, a.epoch);
+        // outputs: beta, R_cc; 1/v0 for the vector
+        st_md<P>(a.beta, a.beta_ps, c, finite ? xf_to_md<P, N>(bet) : md_from_double<P>(dnan()));
+        st_md<P>(colc, ps, c, finite ? xf_to_md<P, N>(rcc) : md_from_double<P>(dnan()));
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh_x[k] = inv.d[k];
+        sh_x[N] = inv.e;
+    }
+    __syncthreads();
+
+    // 4. write back: R above the diagonal, v = u / v0 below it
+    xf<N> inv;
+#pragma unroll
+    for (int k = 0; k < N; ++k) inv.d[k] = sh_x[k];
+    inv.e = sh_x[N];
+    for (int64_t i = tid; i < r; i += NT) {
+        if (i == c) continue;
+        int32_t x[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[k] = Fc[k * fs + i];
+        md<P> y;
+        if (!finite) y = md_from_double<P>(dnan());
+        else if (i < c) y = xf_to_md<P, N>(xf_from_fixed<N, D>(x, ec));
+        else y = xf_to_md<P, N>(xf_mul<N>(xf_from_fixed<N, D>(x, eu_c), inv));
+        st_md<P>(colc, ps, i, y);
+    }
+}
+
+}  // namespace mdls
