@@ -169,7 +169,7 @@ def run_reference(args):
     if rank != 0:
         barrier(world)
         return
-    n_sample = 192
+    n_sample = 256
     for _ in range(args.warmup):
         cpu_baseline(n_sample, precs)
     vals, secs = [], 0.0
@@ -374,7 +374,7 @@ def run_gpu(args):
         out["batched"] = run_batched(args, dev, stream, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(128, precs)
+        out["cpu_baseline"] = cpu_baseline(384, precs)
         out["cpu_baseline"].pop("seconds", None)
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -35,14 +35,19 @@ DEV_INLINE void st_md(double* __restrict__ ptr, int64_t ps, int64_t off, const m
 // Operand views for the md GEMM.  get(i, k, l) returns limb l of element
 // (i, k) of the operand as the GEMM sees it.
 // kRowContig: consecutive i are consecutive in memory (column-major rows).
+// Known zero structure, used by the products to skip k ranges that only meet
+// zeros: kZeroKBelowI (element (i, k) = 0 for k < i, upper triangular) and
+// kZeroKAboveI (element (i, k) = 0 for k > i, lower triangular / trapezoid).
 struct ViewDense {      // X(i, k)
     static constexpr bool kRowContig = true;
+    static constexpr bool kZeroKBelowI = false, kZeroKAboveI = false;
     const double* ptr;
     int64_t ld, ps;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const { return ptr[l * ps + k * ld + i]; }
 };
 struct ViewDenseT {     // X(k, i): the transpose
     static constexpr bool kRowContig = false;
+    static constexpr bool kZeroKBelowI = false, kZeroKAboveI = false;
     const double* ptr;
     int64_t ld, ps;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const { return ptr[l * ps + i * ld + k]; }
@@ -51,6 +56,7 @@ struct ViewDenseT {     // X(k, i): the transpose
 // Y(i, k) = 0 for i < k, 1 for i == k, stored value for i > k.
 struct ViewTrap {
     static constexpr bool kRowContig = true;
+    static constexpr bool kZeroKBelowI = false, kZeroKAboveI = true;
     const double* ptr;  // points at the panel's (0, 0)
     int64_t ld, ps;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const {
@@ -60,6 +66,7 @@ struct ViewTrap {
 };
 struct ViewTrapT {      // Y^T
     static constexpr bool kRowContig = false;
+    static constexpr bool kZeroKBelowI = true, kZeroKAboveI = false;
     const double* ptr;
     int64_t ld, ps;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const {
@@ -70,10 +77,22 @@ struct ViewTrapT {      // Y^T
 // Upper triangular operand (entries below the diagonal read as zero).
 struct ViewUpper {
     static constexpr bool kRowContig = true;
+    static constexpr bool kZeroKBelowI = true, kZeroKAboveI = false;
     const double* ptr;
     int64_t ld, ps;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const {
         return (i <= k) ? ptr[l * ps + k * ld + i] : 0.0;
+    }
+};
+// Transpose of an upper triangular matrix X: element (i, k) = X(k, i), zero
+// for k > i.
+struct ViewUpperT {
+    static constexpr bool kRowContig = false;
+    static constexpr bool kZeroKBelowI = false, kZeroKAboveI = true;
+    const double* ptr;
+    int64_t ld, ps;
+    DEV_INLINE double get(int64_t i, int64_t k, int l) const {
+        return (k <= i) ? ptr[l * ps + i * ld + k] : 0.0;
     }
 };
 

@@ -83,21 +83,30 @@ int launch_split_gemm(int stage, cudaStream_t st, const TcBuf& tc, int64_t M, in
     return MDLS_OK;
 }
 
-// One md matrix-vector product (N = 1), split along K when the rows alone
-// would leave SMs idle.
+// One md matrix-vector product (N = 1).  Rows contiguous in memory: 32 rows
+// per block on the lanes, k split over the block's warps and, when the rows
+// alone would leave SM sub-partitions idle, over grid.y (partials in `sb`,
+// added in a fixed order).  Otherwise one warp per row, lanes along k.
 template <int P, class AV, class BV>
 int launch_gemv(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t K, AV a, BV b, Dense c,
                 bool neg, bool acc) {
+    if (M <= 0) return MDLS_OK;
     StageScope sc(stage, st);
-    constexpr bool rows = AV::kRowContig;
-    const int64_t per_block = rows ? 128 : 4;  // rows per 128-thread block
-    const int64_t blocks = (M + per_block - 1) / per_block;
-    const int64_t target = 2 * (int64_t)sm_count();
+    const int64_t target = 4 * (int64_t)sm_count();  // warps: one per SM sub-partition
     int64_t S = 1;
-    if (blocks < target && K >= 64 && sb.ptr != nullptr) {
-        S = (target + blocks - 1) / blocks;
+    int64_t blocks, warps_per_block;
+    if constexpr (AV::kRowContig) {
+        blocks = (M + 31) / 32;
+        warps_per_block = 4;
+    } else {
+        blocks = (M + 3) / 4;
+        warps_per_block = 4;
+    }
+    const int64_t minK = AV::kRowContig ? 2 * warps_per_block : 64;
+    if (blocks * warps_per_block < target && K >= 2 * minK && sb.ptr != nullptr) {
+        S = (target + blocks * warps_per_block - 1) / (blocks * warps_per_block);
         if (S > 16) S = 16;
-        if (S > K / 32) S = K / 32;
+        if (S > K / minK) S = K / minK;
         while (S > 1 && S * M > sb.cap) --S;
     }
     int64_t kchunk = K > 0 ? K : 1;
@@ -108,14 +117,37 @@ int launch_gemv(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t K, A
     dim3 grid((unsigned)blocks, (unsigned)S);
     Dense out = S > 1 ? Dense{sb.ptr, M, sb.cap} : c;
     const int n_ = S > 1 ? 0 : (neg ? 1 : 0), a_ = S > 1 ? 0 : (acc ? 1 : 0);
-    if (rows)
-        gemv_rows_kernel<P, AV, BV><<<grid, 128, 0, st>>>(M, K, a, b, out, n_, a_, kchunk, M);
+    if constexpr (AV::kRowContig)
+        gemv_kpar_kernel<P, 4, AV, BV><<<grid, 128, 0, st>>>(M, K, a, b, out, n_, a_, kchunk, M);
     else
         gemv_warps_kernel<P, AV, BV><<<grid, 128, 0, st>>>(M, K, a, b, out, n_, a_, kchunk, M);
     MDLS_LAUNCH_CHECK();
     if (S > 1) {
         split_reduce_kernel<P><<<(unsigned)((M + 127) / 128), 128, 0, st>>>(M, 1, (int)S, sb.ptr, M, sb.cap, M,
                                                                           c, neg ? 1 : 0, acc ? 1 : 0);
+        MDLS_LAUNCH_CHECK();
+    }
+    return MDLS_OK;
+}
+
+// The levels of the recursive combination X12 = -X1 M12 X2 (kernels.cuh) for
+// `ntiles` tiles of width t (the last one min(t, n - (ntiles-1) t)), whose
+// leaves of size L are already in place: block sizes s = L, 2L, ... < t, two
+// launches per level for all pairs of all tiles.
+template <int P>
+int tri_levels(int stage, cudaStream_t st, double* X, int64_t ldx, int64_t psx, int64_t xtile,
+               const double* M, int64_t ldm, int64_t psm, int64_t mtile, int64_t n, int t,
+               int64_t ntiles, int L) {
+    StageScope sc(stage, st);
+    for (int s = L; s < t; s *= 2) {
+        int KS = 1;
+        while (KS * 16 < s && KS < 4) KS *= 2;
+        const int nbs = (s + 7) / 8;
+        dim3 grid((unsigned)(nbs * nbs), (unsigned)((t + 2 * s - 1) / (2 * s)), (unsigned)ntiles);
+        const size_t smem = (size_t)KS * 64 * sizeof(md<P>);
+        tri_level_kernel<P, 0><<<grid, 64 * KS, smem, st>>>(X, ldx, psx, xtile, M, ldm, psm, mtile, n, t, s);
+        MDLS_LAUNCH_CHECK();
+        tri_level_kernel<P, 1><<<grid, 64 * KS, smem, st>>>(X, ldx, psx, xtile, M, ldm, psm, mtile, n, t, s);
         MDLS_LAUNCH_CHECK();
     }
     return MDLS_OK;
@@ -137,8 +169,9 @@ int launch_gemm(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t N, i
     }
     if (N == 1 && !upper_only) return launch_gemv<P>(stage, st, sb, M, K, a, b, c, neg, acc);
     StageScope sc(stage, st);
-    const int64_t gx = (M + kGemmTile - 1) / kGemmTile, gy = (N + kGemmTile - 1) / kGemmTile;
-    const int64_t tiles = upper_only ? (gx * (gx + 1)) / 2 : gx * gy;
+    constexpr int TN = gemm_tn<P>();
+    const int64_t gx = (M + kGemmTile - 1) / kGemmTile, gy = (N + TN - 1) / TN;
+    const int64_t tiles = upper_only ? (gx * gy + gx) / 2 : gx * gy;
     const int64_t target = 2 * (int64_t)sm_count();
     int64_t S = 1;
     if (tiles < target && K >= 4 * kGemmTile && sb.ptr != nullptr) {
@@ -156,14 +189,14 @@ int launch_gemm(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t N, i
     if (K <= 0) kchunk = 1;
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)S);
     if (S == 1) {
-        gemm_kernel<P, AV, BV><<<grid, kGemmTile * kGemmTile, 0, st>>>(
+        gemm_kernel<P, AV, BV><<<grid, kGemmTile * TN, 0, st>>>(
             M, N, K, a, b, c, neg ? 1 : 0, acc ? 1 : 0, kchunk, 0, upper_only ? 1 : 0);
         MDLS_LAUNCH_CHECK();
         return MDLS_OK;
     }
     Dense part{sb.ptr, M, sb.cap};
-    gemm_kernel<P, AV, BV><<<grid, kGemmTile * kGemmTile, 0, st>>>(M, N, K, a, b, part, 0, 0, kchunk,
-                                                                    M * N, upper_only ? 1 : 0);
+    gemm_kernel<P, AV, BV><<<grid, kGemmTile * TN, 0, st>>>(M, N, K, a, b, part, 0, 0, kchunk,
+                                                             M * N, upper_only ? 1 : 0);
     MDLS_LAUNCH_CHECK();
     const int64_t total = M * N;
     split_reduce_kernel<P><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(
@@ -254,9 +287,12 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
         int rc = launch_gemm<P>(ST_W, st, sb, w, w, r, Yt, Y, Dense{G, t, tt2}, false, false, true);
         if (rc) return rc;
         {
+            const int L = w < kTriLeaf ? w : kTriLeaf;
             StageScope sc(ST_W, st);
-            wy_t_kernel<P><<<(unsigned)((w + 3) / 4), 128, 0, st>>>(G, t, tt2, beta, t, w, T, t, tt2);
+            wy_t_leaf_kernel<P><<<(unsigned)((w + 7) / 8), 128, 0, st>>>(G, t, tt2, beta, t, w, L, T, t, tt2);
             MDLS_LAUNCH_CHECK();
+            rc = tri_levels<P>(ST_W, st, T, t, tt2, 0, G, t, tt2, 0, w, w, 1, L);
+            if (rc) return rc;
         }
         double* Wk = (want_q || keep_w) ? (Wb + j0 * ldw + j0) : Wb;
         rc = launch_gemm<P>(ST_W, st, sb, r, w, w, Y, ViewUpper{T, t, tt2}, Dense{Wk, ldw, psw}, true, false);
@@ -304,21 +340,27 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
 }
 
 // Tiled back substitution (Algorithm 1) of R x = y, R upper triangular n x n.
-// Step 1: invert the N diagonal tiles into D.
+// Step 1: invert the N diagonal tiles into D (tile i at D + i t^2, ld t):
+// leaves of 16 columns, then the recursive levels, all tiles at once.
 template <int P>
 int bs_invert(int64_t n, const double* R, int64_t ldr, int64_t psr, int t, char* ws,
               const BsLayout& L, WsHeader* hdr, cudaStream_t st) {
     const int64_t N = (n + t - 1) / t;
     const int64_t tt2 = (int64_t)t * t;
     double* D = reinterpret_cast<double*>(ws + L.D);
-    StageScope sc(ST_INV, st);
-    tri_inv_kernel<P><<<(unsigned)((N * t + 3) / 4), 128, 0, st>>>(R, ldr, psr, n, t, N, D, t,
-                                                                     N * tt2, tt2, hdr);
-    MDLS_LAUNCH_CHECK();
-    return MDLS_OK;
+    const int leaf = t < kTriLeaf ? t : kTriLeaf;
+    {
+        StageScope sc(ST_INV, st);
+        const int64_t warps = N * ((t + 1) / 2);
+        tri_leaf_inv_kernel<P><<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(R, ldr, psr, n, t, leaf, N, D, t,
+                                                                            N * tt2, tt2, hdr);
+        MDLS_LAUNCH_CHECK();
+    }
+    return tri_levels<P>(ST_INV, st, D, t, N * tt2, tt2, R, ldr, psr, (int64_t)t * (ldr + 1), n, t, N, leaf);
 }
 
-// Step 2: i = N..1, x_i := U_i^{-1} y_i, then y_j -= A_{j,i} x_i for all j < i.
+// Step 2: i = N..1, x_i := U_i^{-1} y_i, then y_j -= A_{j,i} x_i for all j < i
+// (both as split matrix-vector products).
 template <int P>
 int bs_solve(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y, int64_t psy,
              double* x, int64_t psx, int t, char* ws, const BsLayout& L, cudaStream_t st) {
@@ -326,6 +368,7 @@ int bs_solve(int64_t n, const double* R, int64_t ldr, int64_t psr, const double*
     const int64_t tt2 = (int64_t)t * t;
     double* D = reinterpret_cast<double*>(ws + L.D);
     double* bw = reinterpret_cast<double*>(ws + L.b);
+    const SplitBuf sbp{reinterpret_cast<double*>(ws + L.part), kBsPartCap};
     const int64_t dps = N * tt2;
     for (int l = 0; l < P; ++l)
         if (cudaMemcpyAsync(bw + l * n, y + l * psy, n * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -334,16 +377,13 @@ int bs_solve(int64_t n, const double* R, int64_t ldr, int64_t psr, const double*
     for (int64_t i = N - 1; i >= 0; --i) {
         const int64_t o = i * t;
         const int tt = (int)((n - o) < t ? (n - o) : t);
-        {
-            StageScope sc(ST_MULINV, st);
-            bs_mulinv_kernel<P><<<1, t, 0, st>>>(D + i * tt2, t, dps, tt, bw, n, x, psx, o);
-            MDLS_LAUNCH_CHECK();
-        }
+        int rc = launch_gemv<P>(ST_MULINV, st, sbp, tt, tt, ViewUpper{D + i * tt2, t, dps},
+                                ViewDense{bw + o, n, n}, Dense{x + o, n, psx}, false, false);
+        if (rc) return rc;
         if (o > 0) {
-            StageScope sc(ST_BSUPD, st);
-            bs_update_kernel<P><<<(unsigned)((o + 127) / 128), 128, 0, st>>>(R, ldr, psr, o, tt, x,
-                                                                           psx, bw, n);
-            MDLS_LAUNCH_CHECK();
+            rc = launch_gemv<P>(ST_BSUPD, st, sbp, o, tt, ViewDense{R + o * ldr, ldr, psr},
+                                ViewDense{x + o, n, psx}, Dense{bw, n, n}, true, true);
+            if (rc) return rc;
         }
     }
     return MDLS_OK;
@@ -382,7 +422,9 @@ int apply_qt(int64_t m, int64_t n, int t, const double* A, int64_t psa, const do
 }
 
 // Solves R^T h = g (R upper triangular n x n, its diagonal tiles inverted in
-// L.D by bs_invert): the block forward substitution of the transposed system.
+// L.D by bs_invert): the block forward substitution of the transposed system,
+// h_i := (U_i^{-1})^T g_i, then g_j := g_j - (R_ij)^T h_i for the rows after
+// tile i.
 template <int P>
 int fs_solve(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* g, int64_t psg,
              double* h, int64_t psh, int t, char* ws, const BsLayout& L, int stage, cudaStream_t st) {
@@ -390,6 +432,7 @@ int fs_solve(int64_t n, const double* R, int64_t ldr, int64_t psr, const double*
     const int64_t tt2 = (int64_t)t * t;
     const double* D = reinterpret_cast<const double*>(ws + L.D);
     double* gw = reinterpret_cast<double*>(ws + L.b);
+    const SplitBuf sbp{reinterpret_cast<double*>(ws + L.part), kBsPartCap};
     for (int l = 0; l < P; ++l)
         if (cudaMemcpyAsync(gw + l * n, g + l * psg, n * sizeof(double), cudaMemcpyDeviceToDevice,
                             st) != cudaSuccess)
@@ -397,17 +440,14 @@ int fs_solve(int64_t n, const double* R, int64_t ldr, int64_t psr, const double*
     for (int64_t i = 0; i < N; ++i) {
         const int64_t o = i * t;
         const int tt = (int)((n - o) < t ? (n - o) : t);
-        {
-            StageScope sc(stage, st);
-            fs_mulinv_t_kernel<P><<<1, t, 0, st>>>(D + i * tt2, t, N * tt2, tt, gw, n, h, psh, o);
-            MDLS_LAUNCH_CHECK();
-        }
+        int rc = launch_gemv<P>(stage, st, sbp, tt, tt, ViewUpperT{D + i * tt2, t, N * tt2},
+                                ViewDense{gw + o, n, n}, Dense{h + o, n, psh}, false, false);
+        if (rc) return rc;
         const int64_t rest = n - o - tt;
         if (rest > 0) {
-            StageScope sc(stage, st);
-            fs_update_kernel<P><<<(unsigned)((rest + 127) / 128), 128, 0, st>>>(R, ldr, psr, o, tt, n, h,
-                                                                              psh, gw, n);
-            MDLS_LAUNCH_CHECK();
+            rc = launch_gemv<P>(stage, st, sbp, rest, tt, ViewDenseT{R + (o + tt) * ldr + o, ldr, psr},
+                                ViewDense{h + o, n, psh}, Dense{gw + o + tt, n, n}, true, true);
+            if (rc) return rc;
         }
     }
     return MDLS_OK;

@@ -51,6 +51,38 @@ DEV_INLINE md<P> warp_sum(md<P> x) {
     return x;
 }
 
+// Deterministic sum over the 16 lanes of each half warp (fixed shfl_down tree
+// ending in the half's first lane, then broadcast within the half).
+template <int P>
+DEV_INLINE md<P> half_sum(md<P> x) {
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+        md<P> y;
+#pragma unroll
+        for (int l = 0; l < P; ++l) y.v[l] = __shfl_down_sync(0xffffffffu, x.v[l], off, 16);
+        x = md_add<P>(x, y);
+    }
+#pragma unroll
+    for (int l = 0; l < P; ++l) x.v[l] = __shfl_sync(0xffffffffu, x.v[l], 0, 16);
+    return x;
+}
+
+template <int P>
+DEV_INLINE md<P> half_shfl(const md<P>& x, int src) {
+    md<P> r;
+#pragma unroll
+    for (int l = 0; l < P; ++l) r.v[l] = __shfl_sync(0xffffffffu, x.v[l], src, 16);
+    return r;
+}
+
+template <int P>
+DEV_INLINE md<P> md_select(bool c, const md<P>& a, const md<P>& b) {
+    md<P> r;
+#pragma unroll
+    for (int l = 0; l < P; ++l) r.v[l] = c ? a.v[l] : b.v[l];
+    return r;
+}
+
 constexpr long long kFlagTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // Householder scalars of x = (x0, x_1..): sigma = sum_{i>0} x_i^2 given.
@@ -223,36 +255,58 @@ __global__ void __launch_bounds__(NT) panel_rows_kernel(RowPanelArgs a) {
 
 // ----------------------------------------------------------------------------
 // md GEMM: C(i,j) = [C(i,j)] +/- sum_k A(i,k) B(k,j), one output per thread,
-// 16x16 output tile per block, operands staged limb-planar in shared memory.
-// Used for every product of the WY representation (Section 3):
-// G = Y^T Y, W = -Y T, W^T C, C + Y (W^T C), Y^T Q, Q + W (Y^T Q).
+// a 16 x TN output tile per block, operands staged limb-planar in shared
+// memory.  Used for every product of the WY representation (Section 3):
+// G = Y^T Y, W = -Y T, W^T C, C + Y (W^T C), Y^T Q, Q + W (Y^T Q).  The
+// octo-double instance runs 16 x 8 tiles (128 threads, about 150 registers
+// each) so that three blocks share an SM: the FP64 pipe needs more than two
+// warps per sub-partition to hide the latency of dependent instructions.
 // ----------------------------------------------------------------------------
 constexpr int kGemmTile = 16;
+
+template <int P>
+__host__ __device__ constexpr int gemm_tn() {
+    return P == 8 ? 8 : 16;
+}
 
 // With split-K (gridDim.z > 1) block z sums k in [z kchunk, (z+1) kchunk) and
 // writes its raw partial sum to C.ptr + z * zstride (negate/accumulate are
 // then applied by split_reduce_kernel).  upper_only skips output tiles that
 // lie entirely below the diagonal (symmetric products).
 template <int P, class AV, class BV>
-__global__ void __launch_bounds__(kGemmTile* kGemmTile)
+__global__ void __launch_bounds__(kGemmTile* gemm_tn<P>())
     gemm_kernel(int64_t M, int64_t N, int64_t K, AV A, BV B, Dense C, int negate, int accumulate,
                 int64_t kchunk, int64_t zstride, int upper_only) {
-    __shared__ double As[P][kGemmTile][kGemmTile + 1];
-    __shared__ double Bs[P][kGemmTile][kGemmTile + 1];
+    constexpr int TN = gemm_tn<P>();
+    constexpr int NT = kGemmTile * TN;
+    __shared__ double As[P][kGemmTile][kGemmTile + 1];  // [limb][k][i]
+    __shared__ double Bs[P][TN][kGemmTile + 1];         // [limb][j][k]
     const int tx = threadIdx.x % kGemmTile, ty = threadIdx.x / kGemmTile;
-    const int64_t i0 = (int64_t)blockIdx.x * kGemmTile, j0 = (int64_t)blockIdx.y * kGemmTile;
+    const int64_t i0 = (int64_t)blockIdx.x * kGemmTile, j0 = (int64_t)blockIdx.y * TN;
     const int64_t i = i0 + tx, j = j0 + ty;
-    if (upper_only && i0 > j0 + kGemmTile - 1) return;  // whole block below the diagonal
-    const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
-    const int64_t kend = (kbeg + kchunk) < K ? (kbeg + kchunk) : K;
+    if (upper_only && i0 > j0 + TN - 1) return;  // whole block below the diagonal
+    int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+    int64_t kend = (kbeg + kchunk) < K ? (kbeg + kchunk) : K;
+    // k ranges that only meet known zeros of A (rows i0..) or B (columns j0..)
+    if constexpr (AV::kZeroKBelowI) kbeg = kbeg > i0 ? kbeg : i0;
+    if constexpr (AV::kZeroKAboveI) kend = kend < i0 + kGemmTile ? kend : i0 + kGemmTile;
+    if constexpr (BV::kZeroKBelowI) kend = kend < j0 + TN ? kend : j0 + TN;
+    if constexpr (BV::kZeroKAboveI) kbeg = kbeg > j0 ? kbeg : j0;
     md<P> acc = md_zero<P>();
     for (int64_t k0 = kbeg; k0 < kend; k0 += kGemmTile) {
-        const bool a_in = (i0 + tx < M) && (k0 + ty < kend);
-        const bool b_in = (k0 + tx < kend) && (j0 + ty < N);
 #pragma unroll
-        for (int l = 0; l < P; ++l) {
-            As[l][ty][tx] = a_in ? A.get(i0 + tx, k0 + ty, l) : 0.0;   // A(i0+tx, k0+ty)
-            Bs[l][ty][tx] = b_in ? B.get(k0 + tx, j0 + ty, l) : 0.0;   // B(k0+tx, j0+ty)
+        for (int idx = threadIdx.x; idx < kGemmTile * kGemmTile; idx += NT) {
+            const int ii = idx % kGemmTile, kk = idx / kGemmTile;
+            const bool in = (i0 + ii < M) && (k0 + kk < kend);
+#pragma unroll
+            for (int l = 0; l < P; ++l) As[l][kk][ii] = in ? A.get(i0 + ii, k0 + kk, l) : 0.0;
+        }
+#pragma unroll
+        for (int idx = threadIdx.x; idx < kGemmTile * TN; idx += NT) {
+            const int kk = idx % kGemmTile, jj = idx / kGemmTile;
+            const bool in = (k0 + kk < kend) && (j0 + jj < N);
+#pragma unroll
+            for (int l = 0; l < P; ++l) Bs[l][jj][kk] = in ? B.get(k0 + kk, j0 + jj, l) : 0.0;
         }
         __syncthreads();
         const int kmax = (int)((kend - k0) < kGemmTile ? (kend - k0) : kGemmTile);
@@ -279,27 +333,47 @@ __global__ void __launch_bounds__(kGemmTile* kGemmTile)
     }
 }
 
-// Matrix-vector products (N = 1): y(i) = [y] +/- sum_k A(i,k) x(k), with the
-// K range split over grid.y as in gemm_kernel.  gemv_rows_kernel: one thread
-// per row (A contiguous along i); gemv_warps_kernel: one warp per row, lanes
-// along k (A contiguous along k), fixed-order warp reduction.
-template <int P, class AV, class BV>
-__global__ void gemv_rows_kernel(int64_t M, int64_t K, AV A, BV B, Dense C, int negate, int accumulate,
-                                 int64_t kchunk, int64_t zstride) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M) return;
-    const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
-    const int64_t kend = (kbeg + kchunk) < K ? (kbeg + kchunk) : K;
+// Matrix-vector products (N = 1): y(i) = [y] +/- sum_k A(i,k) x(k).
+// gemv_kpar_kernel (A contiguous along i): lanes own 32 consecutive rows
+// (coalesced loads), the NW warps of a block take interleaved k and their
+// partial sums meet in a fixed tree in shared memory; grid.y splits the K
+// range further as in gemm_kernel.  On this GPU an FP64 warp instruction
+// holds its SM sub-partition for 64 cycles whatever the number of active
+// lanes, so short products must be spread over many warps rather than run as
+// long per-thread chains.  gemv_warps_kernel (A contiguous along k): one warp
+// per row, lanes along k, fixed-order warp reduction.
+template <int P, int NW, class AV, class BV>
+__global__ void __launch_bounds__(32 * NW)
+    gemv_kpar_kernel(int64_t M, int64_t K, AV A, BV B, Dense C, int negate, int accumulate,
+                     int64_t kchunk, int64_t zstride) {
+    __shared__ md<P> red[NW][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i0 = (int64_t)blockIdx.x * 32, i = i0 + lane;
+    int64_t kb = (int64_t)blockIdx.y * kchunk;
+    int64_t ke = (kb + kchunk) < K ? (kb + kchunk) : K;
+    if constexpr (AV::kZeroKBelowI) kb = kb > i0 ? kb : i0;
+    if constexpr (AV::kZeroKAboveI) ke = ke < i0 + 32 ? ke : i0 + 32;
     md<P> acc = md_zero<P>();
-    for (int64_t k = kbeg; k < kend; ++k) {
-        md<P> a, x;
+    if (i < M) {
+        for (int64_t k = kb + warp; k < ke; k += NW) {
+            md<P> a, x;
 #pragma unroll
-        for (int l = 0; l < P; ++l) {
-            a.v[l] = A.get(i, k, l);
-            x.v[l] = B.get(k, 0, l);
+            for (int l = 0; l < P; ++l) {
+                a.v[l] = A.get(i, k, l);
+                x.v[l] = B.get(k, 0, l);
+            }
+            acc = md_fma<P>(acc, a, x);
         }
-        acc = md_fma<P>(acc, a, x);
     }
+    red[warp][lane] = acc;
+    __syncthreads();
+#pragma unroll
+    for (int h = NW / 2; h > 0; h >>= 1) {
+        if (warp < h) red[warp][lane] = md_add<P>(red[warp][lane], red[warp + h][lane]);
+        __syncthreads();
+    }
+    if (warp != 0 || i >= M) return;
+    acc = red[0][lane];
     if (gridDim.y > 1) {
         st_md<P>(C.ptr + blockIdx.y * zstride, C.ps, i, acc);
         return;
@@ -315,8 +389,10 @@ __global__ void gemv_warps_kernel(int64_t M, int64_t K, AV A, BV B, Dense C, int
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= M) return;  // whole warp
-    const int64_t kbeg = (int64_t)blockIdx.y * kchunk;
-    const int64_t kend = (kbeg + kchunk) < K ? (kbeg + kchunk) : K;
+    int64_t kbeg = (int64_t)blockIdx.y * kchunk;
+    int64_t kend = (kbeg + kchunk) < K ? (kbeg + kchunk) : K;
+    if constexpr (AV::kZeroKBelowI) kbeg = kbeg > i ? kbeg : i;
+    if constexpr (AV::kZeroKAboveI) kend = kend < i + 1 ? kend : i + 1;
     md<P> acc = md_zero<P>();
     for (int64_t k = kbeg + lane; k < kend; k += 32) {
         md<P> a, x;
@@ -355,135 +431,147 @@ __global__ void split_reduce_kernel(int64_t M, int64_t N, int S, const double* p
 }
 
 // ----------------------------------------------------------------------------
-// Inversion of upper triangular tiles: step 1 of Algorithm 1.  Diagonal tile
-// i covers rows/cols o..o+tt-1 of U (o = i t).  Column k of its inverse
-// solves U v = e_k: v_k = 1/U_kk and, for l = k-1 down to 0,
-// v_l = -(sum_{s=l+1}^{k} U_ls v_s) / U_ll.  The paper gives each column to
-// one thread; here one warp solves one column, its lanes splitting each sum
-// (fixed-order reduction), and grid.x * blockDim/32 warps cover the N*t
-// columns.  A zero pivot records MDLS_ERR_SINGULAR.  The inverse is written
-// upper triangular with zeros below the diagonal, tile i at D + i * dtile,
-// column-major with leading dimension dld.
+// Inversion of upper triangular tiles (step 1 of Algorithm 1) and T of the WY
+// form (Section 3), both as a recursion on 2 x 2 block upper triangular
+// matrices.  For X = [X1 X12; 0 X2]:
+//   inverse of U:    X12 = -inv(U1) U12 inv(U2),
+//   T of the WY form (Elmroth and Gustavson): T12 = -T1 (Y1^T Y2) T2,
+// i.e. the same combination X12 = -X1 M12 X2 with M12 the off-diagonal block
+// of U, or of G = Y^T Y.  Leaves of size L <= 16 are solved directly; every
+// level doubles the block size with two small products.  The paper inverts
+// each diagonal tile with one thread per column and builds W column by column;
+// here every serial chain is at most L - 1 steps long and the rest runs as
+// parallel products, which matters on a GPU whose FP64 pipe retires one warp
+// instruction per 64 cycles per SM sub-partition.
 // ----------------------------------------------------------------------------
+constexpr int kTriLeaf = 16;
+
+// Leaves of the tile inversion: column c of the inverse of an L x L diagonal
+// block (leaf) of tile `tile` solves U v = e_c by back substitution,
+// v_c = 1/U_cc and v_l = -(sum_{q=l+1}^{c} U_lq v_q) / U_ll for l < c.  Two
+// columns per warp, one per half; lane h of a half holds v_h and the
+// reciprocal of U_hh (computed once, in parallel).  A zero pivot records
+// MDLS_ERR_SINGULAR (its reciprocal reads as zero).  Column c of tile `tile`
+// goes to D + tile * dtile + c * dld (rows of its leaf only).
 template <int P>
-__global__ void tri_inv_kernel(const double* U, int64_t ld, int64_t ps, int64_t n, int t,
-                               int64_t ntiles, double* D, int64_t dld, int64_t dps, int64_t dtile,
-                               WsHeader* hdr) {
+__global__ void tri_leaf_inv_kernel(const double* U, int64_t ld, int64_t ps, int64_t n, int t, int L,
+                                    int64_t ntiles, double* D, int64_t dld, int64_t dps, int64_t dtile,
+                                    WsHeader* hdr) {
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= ntiles * t) return;  // whole warp
-    const int64_t tile = gw / t;
-    const int k = (int)(gw % t);
+    const int lane = threadIdx.x & 31, half = lane >> 4, h = lane & 15;
+    const int64_t ppt = (t + 1) / 2;  // column pairs per tile
+    if (gw >= ntiles * ppt) return;   // whole warp
+    const int64_t tile = gw / ppt;
+    const int c0 = 2 * (int)(gw % ppt);
     const int64_t o = tile * t;
     const int tt = (int)((n - o) < t ? (n - o) : t);
-    const double* Ut = U + o * ld + o;
-    double* col = D + tile * dtile + (int64_t)k * dld;
-    if (k >= tt) {
-        for (int l = lane; l < t; l += 32) st_md<P>(col, dps, l, md_zero<P>());
-        return;
-    }
-    for (int l = k + 1 + lane; l < t; l += 32) st_md<P>(col, dps, l, md_zero<P>());
-    if (lane == 0) {
-        md<P> d = ld_md<P>(Ut, ps, (int64_t)k * ld + k);
+    if (c0 >= tt) return;  // whole warp
+    const int c = c0 + half;
+    const bool valid = c < tt;
+    const int leaf0 = (c0 / L) * L;
+    const int le = (leaf0 + L) < tt ? (leaf0 + L) : tt;
+    const int k = c - leaf0;
+    const double* Ul = U + (o + leaf0) * ld + (o + leaf0);
+    md<P> r = md_zero<P>();
+    if (leaf0 + h < le) {
+        const md<P> d = ld_md<P>(Ul, ps, (int64_t)h * ld + h);
         if (d.v[0] == 0.0) set_status(&hdr->status, MDLS_ERR_SINGULAR);
-        st_md<P>(col, dps, k, d.v[0] == 0.0 ? md_zero<P>() : md_div<P>(md_one<P>(), d));
+        else r = md_div<P>(md_one<P>(), d);
     }
-    __syncwarp();
-    for (int l = k - 1; l >= 0; --l) {
-        md<P> s = md_zero<P>();
-        for (int q = l + 1 + lane; q <= k; q += 32)
-            s = md_fma<P>(s, ld_md<P>(Ut, ps, (int64_t)q * ld + l), ld_md<P>(col, dps, q));
-        s = warp_sum<P>(s);
-        if (lane == 0) {
-            md<P> d = ld_md<P>(Ut, ps, (int64_t)l * ld + l);
-            if (d.v[0] == 0.0) {
-                set_status(&hdr->status, MDLS_ERR_SINGULAR);
-                st_md<P>(col, dps, l, md_zero<P>());
-            } else {
-                st_md<P>(col, dps, l, md_neg<P>(md_div<P>(s, d)));
-            }
+    md<P> v = (valid && h == k) ? r : md_zero<P>();
+    const int kw = ((c0 + 1) < tt ? (c0 + 1) : c0) - leaf0;  // largest column of the warp
+    for (int l = kw - 1; l >= 0; --l) {
+        const bool act = valid && l < k;
+        const bool in = act && h > l && h <= k;
+        const md<P> u = in ? ld_md<P>(Ul, ps, (int64_t)h * ld + l) : md_zero<P>();
+        const md<P> sum = half_sum<P>(md_mul<P>(u, v));
+        const md<P> vl = md_neg<P>(md_mul<P>(sum, half_shfl<P>(r, l)));
+        v = md_select<P>(act && h == l, vl, v);
+    }
+    if (valid && h <= k) st_md<P>(D + tile * dtile + (int64_t)c * dld, dps, leaf0 + h, v);
+}
+
+// Leaves of T: inside each L x L diagonal block, row l of T has T[l,l] =
+// beta_l and T[l,j] = -beta_j sum_{q=l}^{j-1} T[l,q] G[q,j] for l < j < the
+// leaf's end (G = Y^T Y), so that H_1 ... H_w = I - Y T Y^T = I + W Y^T with
+// W = -Y T: the paper's z_j = -beta_j (v_j + W Y^T v_j), with Y^T v read
+// from G.  Two rows per warp, one per half; lane h holds T[l, leaf0 + h].  An
+// identity reflector (beta_j = 0) gives a zero column j.
+template <int P>
+__global__ void wy_t_leaf_kernel(const double* G, int64_t ldg, int64_t psg, const double* beta,
+                                 int64_t bps, int w, int L, double* T, int64_t ldt, int64_t pst) {
+    const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31, half = lane >> 4, h = lane & 15;
+    const int l0 = 2 * gw;
+    if (l0 >= w) return;  // whole warp
+    const int l = l0 + half;
+    const bool valid = l < w;
+    const int leaf0 = (l0 / L) * L;
+    const int le = (leaf0 + L) < w ? (leaf0 + L) : w;
+    const int q = leaf0 + h;
+    md<P> tv = (valid && q == l) ? ld_md<P>(beta, bps, l) : md_zero<P>();
+    for (int j = l0 + 1; j < le; ++j) {
+        const bool act = valid && j > l;
+        const bool in = act && q >= l && q < j;
+        const md<P> g = in ? ld_md<P>(G, psg, (int64_t)j * ldg + q) : md_zero<P>();
+        const md<P> sum = half_sum<P>(md_mul<P>(in ? tv : md_zero<P>(), g));
+        const md<P> tj = md_neg<P>(md_mul<P>(ld_md<P>(beta, bps, j), sum));
+        tv = md_select<P>(act && q == j, tj, tv);
+    }
+    if (valid && q >= l && q < le) st_md<P>(T, pst, (int64_t)q * ldt + l, tv);
+}
+
+// One level of the recursion for all pairs of all tiles: tile b (width
+// min(t, n - b t), at X + b xtile and M + b mtile) pairs its blocks
+// X1 = X[a:a+s, a:a+s] and X2 = X[a+s:a+s+s2, a+s:a+s+s2] (a = 2 s y).
+//   STEP 0: Z = M12 X2 (X2 upper triangular: k <= j), kept in the unused
+//           lower block of X as X[a+s+j, a+i] = Z(i, j);
+//   STEP 1: X12 = -X1 Z (X1 upper triangular: k >= i) into X[a+i, a+s+j].
+// An 8 x 8 output block per 64 threads; the k range is split over
+// blockDim.x / 64 (at most 4) groups whose partial sums meet in a fixed tree.
+template <int P, int STEP>
+__global__ void __launch_bounds__(256) tri_level_kernel(double* X, int64_t ldx, int64_t psx, int64_t xtile, const double* M,
+                                 int64_t ldm, int64_t psm, int64_t mtile, int64_t n, int t, int s) {
+    extern __shared__ __align__(16) unsigned char tl_smem[];
+    md<P>* red = reinterpret_cast<md<P>*>(tl_smem);
+    const int KS = blockDim.x >> 6;
+    const int tid = threadIdx.x & 63, kz = threadIdx.x >> 6;
+    const int nbs = (s + 7) >> 3;
+    const int i = (blockIdx.x % nbs) * 8 + (tid & 7), j = (blockIdx.x / nbs) * 8 + (tid >> 3);
+    const int64_t b = blockIdx.z;
+    const int64_t a = (int64_t)blockIdx.y * 2 * s;
+    const int64_t tt = (n - b * t) < t ? (n - b * t) : t;
+    if (a + s >= tt) return;  // whole block: this pair has no second block
+    const int s2 = (int)((tt - a - s) < s ? (tt - a - s) : s);
+    double* Xb = X + b * xtile;
+    const double* Mb = M + b * mtile;
+    const bool out = i < s && j < s2;
+    md<P> acc = md_zero<P>();
+    if (out) {
+        const int kc = (s + KS - 1) / KS;
+        int kb = kz * kc, ke = kb + kc;
+        if (STEP == 0) {
+            ke = ke < j + 1 ? ke : j + 1;
+            for (int k = kb; k < ke; ++k)
+                acc = md_fma<P>(acc, ld_md<P>(Mb, psm, (a + s + k) * ldm + a + i),
+                                ld_md<P>(Xb, psx, (a + s + j) * ldx + a + s + k));
+        } else {
+            kb = kb > i ? kb : i;
+            ke = ke < s ? ke : s;
+            for (int k = kb; k < ke; ++k)
+                acc = md_fma<P>(acc, ld_md<P>(Xb, psx, (a + k) * ldx + a + i),
+                                ld_md<P>(Xb, psx, (a + k) * ldx + a + s + j));
         }
-        __syncwarp();
     }
-}
-
-// T of the WY representation of one tile.  With G = Y^T Y and the betas of
-// the panel, T_jj = beta_j and T[l, j] = -beta_j sum_{q=l}^{j-1} T[l, q] G[q, j]
-// for l < j, so that H_1 ... H_w = I - Y T Y^T = I + W Y^T with W = -Y T.
-// Column j of W is then z_j = -beta_j (v_j + W_{:,<j} (Y_{:,<j}^T v_j)): the
-// paper's formula for z (Section 3), with the products Y^T v read from G.
-// Row l of T depends only on its own earlier entries: one warp builds row l,
-// its lanes splitting the sum over q (fixed-order reduction).  An identity
-// reflector (beta_j = 0) gives a zero column j, as it must.
-template <int P>
-__global__ void wy_t_kernel(const double* G, int64_t ldg, int64_t psg, const double* beta,
-                            int64_t bps, int w, double* T, int64_t ldt, int64_t pst) {
-    const int l = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (l >= w) return;  // whole warp
-    if (lane == 0) st_md<P>(T, pst, (int64_t)l * ldt + l, ld_md<P>(beta, bps, l));
-    __syncwarp();
-    for (int j = l + 1; j < w; ++j) {
-        md<P> s = md_zero<P>();
-        for (int q = l + lane; q < j; q += 32)
-            s = md_fma<P>(s, ld_md<P>(T, pst, (int64_t)q * ldt + l), ld_md<P>(G, psg, (int64_t)j * ldg + q));
-        s = warp_sum<P>(s);
-        if (lane == 0)
-            st_md<P>(T, pst, (int64_t)j * ldt + l, md_neg<P>(md_mul<P>(ld_md<P>(beta, bps, j), s)));
-        __syncwarp();
+    red[kz * 64 + tid] = acc;
+    __syncthreads();
+    for (int hh = KS / 2; hh > 0; hh >>= 1) {
+        if (kz < hh) red[kz * 64 + tid] = md_add<P>(red[kz * 64 + tid], red[(kz + hh) * 64 + tid]);
+        __syncthreads();
     }
-}
-
-// Step 2(a) of Algorithm 1: x_i := U_i^{-1} b_i (one block, thread k computes
-// entry k; the inverse tile is upper triangular).
-template <int P>
-__global__ void bs_mulinv_kernel(const double* Dt, int64_t dld, int64_t dps, int tt,
-                                 const double* bw, int64_t bps, double* x, int64_t xps,
-                                 int64_t o) {
-    const int k = threadIdx.x;
-    if (k >= tt) return;
-    md<P> s = md_zero<P>();
-    for (int q = k; q < tt; ++q)
-        s = md_fma<P>(s, ld_md<P>(Dt, dps, (int64_t)q * dld + k), ld_md<P>(bw, bps, o + q));
-    st_md<P>(x, xps, o + k, s);
-}
-
-// Forward substitution with R^T (lower triangular), using the same inverted
-// diagonal tiles: h_i := (U_i^{-1})^T g_i (thread k: sum over q <= k of
-// D(q, k) g(q)), then g_j := g_j - (R_ij)^T h_i for the rows after tile i.
-template <int P>
-__global__ void fs_mulinv_t_kernel(const double* Dt, int64_t dld, int64_t dps, int tt,
-                                   const double* gw, int64_t gps, double* h, int64_t hps, int64_t o) {
-    const int k = threadIdx.x;
-    if (k >= tt) return;
-    md<P> s = md_zero<P>();
-    for (int q = 0; q <= k; ++q)
-        s = md_fma<P>(s, ld_md<P>(Dt, dps, (int64_t)k * dld + q), ld_md<P>(gw, gps, o + q));
-    st_md<P>(h, hps, o + k, s);
-}
-
-template <int P>
-__global__ void fs_update_kernel(const double* U, int64_t ld, int64_t ps, int64_t o, int tt,
-                                 int64_t n, const double* h, int64_t hps, double* gw, int64_t gps) {
-    const int64_t row = o + tt + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= n) return;
-    md<P> s = ld_md<P>(gw, gps, row);
-    const double* Ucol = U + row * ld + o;   // column `row` of R, rows o..o+tt-1
-    for (int q = 0; q < tt; ++q) s = md_fms<P>(s, ld_md<P>(Ucol, ps, q), ld_md<P>(h, hps, o + q));
-    st_md<P>(gw, gps, row, s);
-}
-
-// Step 2(b) of Algorithm 1: b_j := b_j - A_{j,i} x_i for all rows above tile
-// i at once (thread per row).
-template <int P>
-__global__ void bs_update_kernel(const double* U, int64_t ld, int64_t ps, int64_t o, int tt,
-                                 const double* x, int64_t xps, double* bw, int64_t bps) {
-    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= o) return;
-    md<P> s = ld_md<P>(bw, bps, row);
-    const double* Ur = U + o * ld + row;
-    for (int q = 0; q < tt; ++q) s = md_fms<P>(s, ld_md<P>(Ur, ps, (int64_t)q * ld), ld_md<P>(x, xps, o + q));
-    st_md<P>(bw, bps, row, s);
+    if (kz != 0 || !out) return;
+    if (STEP == 0) st_md<P>(Xb, psx, (a + i) * ldx + a + s + j, red[tid]);
+    else st_md<P>(Xb, psx, (a + s + j) * ldx + a + i, md_neg<P>(red[tid]));
 }
 
 // Elementwise md arithmetic (mdls_vec_op).

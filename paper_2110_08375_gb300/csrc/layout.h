@@ -36,8 +36,10 @@ struct QrLayout {
 
 inline int split_slices(int P) { return (53 * P + 12 + 7) / 8; }
 inline int64_t round16(int64_t x) { return (x + 15) / 16 * 16; }
+// Split matrix-vector partial sums of the back substitution (md values).
+constexpr int64_t kBsPartCap = 4096;
 struct BsLayout {
-    size_t D, b;
+    size_t D, b, part;
 };
 struct LsLayout {
     QrLayout qr;
@@ -94,6 +96,7 @@ inline BsLayout bs_layout_at(Bump& B, int P, int64_t n, int t) {
     const int64_t N = (n + t - 1) / t;
     L.D = B.take(d * (size_t)N * t * t);
     L.b = B.take(d * (size_t)n);
+    L.part = B.take(d * (size_t)kBsPartCap);
     return L;
 }
 

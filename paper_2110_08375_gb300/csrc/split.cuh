@@ -38,6 +38,7 @@ constexpr int kSplitTm = 16, kSplitTn = 8, kSplitTk = 16, kSplitPad = 24;
 template <class BV>
 struct ViewTranspose {  // B^T, so that the columns of B are split like rows
     static constexpr bool kRowContig = false;
+    static constexpr bool kZeroKBelowI = BV::kZeroKAboveI, kZeroKAboveI = BV::kZeroKBelowI;
     BV b;
     DEV_INLINE double get(int64_t i, int64_t k, int l) const { return b.get(k, i, l); }
 };
