@@ -35,6 +35,11 @@ if ROOT not in sys.path:
 METRIC = "md QR+backsub TFLOPS (paper op counts) at dd/qd/od"
 PREC_NAMES = {2: "dd", 4: "qd", 8: "od"}
 FP64_PEAK_TOPS = 2 * 152 * 2.07e9 / 1e12   # FP64 pipe: 2 instructions/clk/SM x 152 SMs x 2.07 GHz
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
+# dominant kernel (profiles/gemm_kernel_od_trailing_n1024.md): 67.6 MB + 2.2 MB
+TRAFFIC_BYTES = 69.85e6
+TRAFFIC_LAUNCH = ("gemm_kernel<8, ViewDenseT, ViewDense>, X = W^T C of tile 0 (128 x 897, K 1024): "
+                  "algorithmic 74.5e6 bytes")
 
 
 def parse():
@@ -268,7 +273,9 @@ def run_gpu(args):
     achieved = trail_ops / (trail_ms / 1e3) / 1e12 if trail_ms > 0 else None
     roofline = {"bound": "alu", "kernel": "gemm_kernel (trailing update C += Y (W^T C))",
                 "achieved": achieved, "peak": FP64_PEAK_TOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TOPS if achieved else None, "traffic": None,
+                "frac": achieved / FP64_PEAK_TOPS if achieved else None,
+                "traffic": TRAFFIC_BYTES if n == 1024 and t == 128 else None,
+                "traffic_launch": TRAFFIC_LAUNCH,
                 "op": "one FP64 instruction (DADD, DMUL or DFMA each occupy one FP64 pipe slot)",
                 "peak_source": "FP64 pipe issue rate 2/clk/SM (ncu peak_sustained) x 152 SMs x 2.07 GHz",
                 "dominant_stage": dominant}
