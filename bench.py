@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--no-backsub", action="store_true")
     return ap.parse_args()
 
 
@@ -379,6 +380,8 @@ def run_gpu(args):
     # mdls_lstsq calls (default tile, one reused workspace) on the same stream
     if not args.no_batched:
         out["batched"] = run_batched(args, dev, stream, flush)
+    if not args.no_backsub:
+        out["backsub_qd_17920"] = run_backsub(args, dev, stream, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(384, precs)
@@ -443,6 +446,62 @@ def run_batched(args, dev, stream, flush):
            "tiles_used": sorted(set(tiles))}
     plan.destroy()
     return res
+
+
+def run_backsub(args, dev, stream, flush, p=4, n=17920, t=128):
+    """Back substitution alone (Algorithm 1): quad double, n = 17920, tile 128
+    (140 tiles).  R upper triangular with diagonal U[1,2], strict upper part
+    U[-1,1)/n, lower limbs x_l = x_(l-1) 2^-54 U[-1,1); y U[-1,1).  Generated
+    on the device from torch's seeded generator (10.3 GB would take minutes to
+    draw and copy from the host); same distribution as synth.upper_triangular."""
+    import torch
+
+    import paper_2110_08375_gb300 as mdls
+    from paper_2110_08375_gb300 import opcount
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    R = torch.empty((p, n, n), dtype=torch.float64, device=dev)   # [limb][col][row]
+    R[0].uniform_(-1.0, 1.0, generator=g).div_(n)
+    R[0].diagonal().uniform_(1.0, 2.0, generator=g)
+    for l in range(1, p):
+        R[l].uniform_(-1.0, 1.0, generator=g).mul_(R[l - 1]).mul_(2.0 ** -54)
+    for l in range(p):
+        R[l].copy_(torch.tril(R[l]))   # [col][row] lower = rows above the diagonal: R upper triangular
+    y = torch.empty((p, n), dtype=torch.float64, device=dev)
+    y[0].uniform_(-1.0, 1.0, generator=g)
+    for l in range(1, p):
+        y[l].uniform_(-1.0, 1.0, generator=g).mul_(y[l - 1]).mul_(2.0 ** -54)
+    x = torch.zeros((p, n), dtype=torch.float64, device=dev)
+    ws = mdls.workspace(mdls.mdls_backsub_workspace(p, n, t), dev)
+    for _ in range(2):
+        mdls.mdls_backsub(R, y, x, tile=t, ws=ws)
+    torch.cuda.synchronize()
+    status = mdls.mdls_read_status(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms = []
+    mdls.mdls_profile_enable(True)
+    mdls.mdls_profile_read()
+    for _ in range(max(args.steps, 3)):
+        flush.zero_()
+        e0.record(stream)
+        mdls.mdls_backsub(R, y, x, tile=t, ws=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    stages = mdls.mdls_profile_read()
+    mdls.mdls_profile_enable(False)
+    k = len(ms)
+    med = statistics.median(ms)
+    flops = opcount.table1_flops(p, opcount.backsub_counts(n))
+    rbytes = n * (n + 1) // 2 * 8 * p
+    del R
+    torch.cuda.empty_cache()
+    return {"workload": f"qd back substitution n={n}, tile {t} ({-(-n // t)} tiles), R resident in HBM, "
+                        "L2 flushed before each solve",
+            "ms": med, "table1_tflops": flops / (med / 1e3) / 1e12,
+            "hbm_gbs_upper_triangle": rbytes / (med / 1e3) / 1e9, "status": status,
+            "stages_ms": {kk: round(v[0] / k, 3) for kk, v in stages.items() if v[0] > 0}}
 
 
 def main():

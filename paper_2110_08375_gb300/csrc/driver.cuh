@@ -16,7 +16,13 @@ constexpr int panel_threads() {
     return P == 8 ? 128 : 256;
 }
 
-constexpr int kFxPanelThreads = 128;  // integer-digit panel: threads per column
+// Integer-digit panel: threads per column.  Octo double keeps 128 (about 170
+// registers each): at 256 threads one block per SM would cap the tile at the
+// SM count.
+template <int P>
+constexpr int fx_panel_threads() {
+    return P == 8 ? 128 : 256;
+}
 
 #define MDLS_LAUNCH_CHECK()                                  \
     do {                                                     \
@@ -211,7 +217,7 @@ int panel_capacity() {
     static int cap = -1;
     if (cap < 0) {
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fx_panel_kernel<P, kFxPanelThreads>, kFxPanelThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fx_panel_kernel<P, fx_panel_threads<P>()>, fx_panel_threads<P>(), 0);
         cap = sm_count() * per;
     }
     return cap;
@@ -273,8 +279,8 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
                 FxPanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, fxF, fxmeta, flags,
                                (unsigned int)(k + 1), hdr};
                 void* args[] = {&pa};
-                if (cudaLaunchCooperativeKernel((const void*)fx_panel_kernel<P, kFxPanelThreads>, dim3(w),
-                                                dim3(kFxPanelThreads), args, 0, st) != cudaSuccess)
+                if (cudaLaunchCooperativeKernel((const void*)fx_panel_kernel<P, fx_panel_threads<P>()>, dim3(w),
+                                                dim3(fx_panel_threads<P>()), args, 0, st) != cudaSuccess)
                     return MDLS_ERR_CUDA;
             }
         }

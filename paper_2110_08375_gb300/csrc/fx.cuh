@@ -390,12 +390,25 @@ FX_CALL int xf_house(const xf<N>& sig, const xf<N>& x0, xf<N>& v0, xf<N>& bp, xf
         beta = bp;
         return 2;
     }
+    // one Newton reciprocal in either branch: R = 1/(mu v0) for x0 <= 0;
+    // for x0 > 0, R = 1/(sigma s) with s = x0 + mu gives 1/s = sigma R and
+    // 1/sigma = s R, so v0 = -sigma^2 R, 1/v0 = -s^2 R, bp = s^2 R / mu
     const xf<N> a2 = xf_add<N>(xf_mul<N>(x0, x0), sig);
-    const xf<N> mu = xf_mul<N>(a2, xf_rsqrt<N>(a2));
-    if (xf_sign(x0) <= 0) v0 = xf_sub<N>(x0, mu);
-    else v0 = xf_neg<N>(xf_mul<N>(sig, xf_recip<N>(xf_add<N>(x0, mu))));
-    bp = xf_neg<N>(xf_recip<N>(xf_mul<N>(mu, v0)));
-    inv_v0 = xf_neg<N>(xf_mul<N>(bp, mu));
+    const xf<N> rs = xf_rsqrt<N>(a2);
+    const xf<N> mu = xf_mul<N>(a2, rs);
+    if (xf_sign(x0) <= 0) {
+        v0 = xf_sub<N>(x0, mu);
+        const xf<N> R = xf_recip<N>(xf_mul<N>(mu, v0));
+        bp = xf_neg<N>(R);
+        inv_v0 = xf_mul<N>(mu, R);
+    } else {
+        const xf<N> sx = xf_add<N>(x0, mu);
+        const xf<N> R = xf_recip<N>(xf_mul<N>(sig, sx));
+        v0 = xf_neg<N>(xf_mul<N>(sig, xf_mul<N>(sig, R)));
+        const xf<N> s2R = xf_mul<N>(sx, xf_mul<N>(sx, R));
+        inv_v0 = xf_neg<N>(s2R);
+        bp = xf_mul<N>(s2R, rs);
+    }
     beta = xf_mul<N>(xf_mul<N>(bp, v0), v0);
     rcc = mu;
     return 0;

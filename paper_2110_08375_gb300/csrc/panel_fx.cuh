@@ -20,6 +20,7 @@
 #pragma once
 #include "common.cuh"
 #include "fx.cuh"
+#include "fxw.cuh"
 #include "kernels.cuh"
 
 namespace mdls {
@@ -48,20 +49,18 @@ struct FxMeta {
     static constexpr int ints = 4 + 2 * N;
 };
 
+// The same record written and read by one warp (digit k by lane k).
 template <int N>
-DEV_INLINE void st_xf(int32_t* p, const fx::xf<N>& x) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) p[k] = x.d[k];
-    p[N] = x.e;
+DEV_INLINE void wst_xf(int32_t* p, const fxw::wxf& x) {
+    const int lane = threadIdx.x & 31;
+    if (lane < N) p[lane] = x.d;
+    if (lane == 0) p[N] = x.e;
 }
 
 template <int N>
-DEV_INLINE fx::xf<N> ld_xf_cg(const int32_t* p) {
-    fx::xf<N> x;
-#pragma unroll
-    for (int k = 0; k < N; ++k) x.d[k] = __ldcg(p + k);
-    x.e = __ldcg(p + N);
-    return x;
+DEV_INLINE fxw::wxf wld_xf_cg(const int32_t* p) {
+    const int lane = threadIdx.x & 31;
+    return fxw::wxf{lane < N ? __ldcg(p + lane) : 0, __ldcg(p + N)};
 }
 
 // Block-wide exact sum of per-thread digit accumulators; the total's digit
@@ -159,6 +158,14 @@ __global__ void __launch_bounds__(NT) fx_panel_kernel(FxPanelArgs a) {
     }
     __syncthreads();
 
+    // sum of squares of the rows below the diagonal and their leading digit
+    int64_t sacc[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) sacc[k] = 0;
+    int top = -1;
+    int cnt = 0;
+    bool fused = false;
+
     // 2. reflectors 0 .. c-1
     for (int ell = 0; ell < c; ++ell) {
         if (tid == 0) sh_i[0] = wait_flag(a.flags + ell, a.epoch, a.hdr) ? 1 : 0;
@@ -186,30 +193,28 @@ __global__ void __launch_bounds__(NT) fx_panel_kernel(FxPanelArgs a) {
         __syncthreads();
         if (!sh_i[1]) return;
         const int kind = __ldcg(a.meta + ell * MI + FxMeta<P>::kKind);
-        // (b) scalars: s = v0 a[ell] + bulk, w = bp s; row ell
-        if (tid == 0) {
-            const xf<N> v0 = ld_xf_cg<N>(a.meta + ell * MI + FxMeta<P>::kV0);
-            const xf<N> bp = ld_xf_cg<N>(a.meta + ell * MI + FxMeta<P>::kBp);
-            int64_t tot[M];
-#pragma unroll
-            for (int k = 0; k < M; ++k) tot[k] = red[0][k];
-            int32_t xe[D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) xe[k] = Fc[k * fs + ell];
-            const xf<N> x_ell = xf_from_fixed<N, D>(xe, ec);
-            const xf<N> s = xf_add<N>(xf_from_acc<N>(tot, eu + ec + D - 3), xf_mul<N>(v0, x_ell));
-            const xf<N> W = xf_mul<N>(bp, s);
-            bool ok = fixed_from_xf<N, D>(xf_sub<N>(x_ell, xf_mul<N>(W, v0)), ec, xe);
-#pragma unroll
-            for (int k = 0; k < D; ++k) Fc[k * fs + ell] = xe[k];
-            int32_t wd[D];
-            if (kind == 0) ok = fixed_from_xf<N, D>(W, ec - eu - (D - 2), wd) && ok;
-            if (!ok) set_status(&a.hdr->status, MDLS_ERR_UNSUPPORTED);
-#pragma unroll
-            for (int k = 0; k < D; ++k) sh_w[k] = kind == 0 ? wd[k] : 0;
+        // (b) scalars: s = v0 a[ell] + bulk, w = bp s; row ell (one warp,
+        //     digit k in lane k: these scalars are on the column chain)
+        if (warp == 0) {
+            const fxw::wxf v0 = wld_xf_cg<N>(a.meta + ell * MI + FxMeta<P>::kV0);
+            const fxw::wxf bp = wld_xf_cg<N>(a.meta + ell * MI + FxMeta<P>::kBp);
+            const int64_t tot = lane < M ? red[0][lane] : 0;
+            const int32_t xe = lane < D ? Fc[lane * fs + ell] : 0;
+            const fxw::wxf x_ell = fxw::from_fixed<N, D>(xe, ec);
+            const fxw::wxf s = fxw::add<N>(fxw::from_acc<N, M>(tot, eu + ec + D - 3), fxw::mul<N>(v0, x_ell));
+            const fxw::wxf W = fxw::mul<N>(bp, s);
+            int32_t xn;
+            bool ok = fxw::fixed_from_xf<N, D>(fxw::sub<N>(x_ell, fxw::mul<N>(W, v0)), ec, xn);
+            if (lane < D) Fc[lane * fs + ell] = xn;
+            int32_t wd = 0;
+            if (kind == 0) ok = fxw::fixed_from_xf<N, D>(W, ec - eu - (D - 2), wd) && ok;
+            if (!ok && lane == 0) set_status(&a.hdr->status, MDLS_ERR_UNSUPPORTED);
+            if (lane < D) sh_w[lane] = kind == 0 ? wd : 0;
         }
         __syncthreads();
-        // rows > ell (a kind-1/2 reflector has no rows below ell)
+        // rows > ell (a kind-1/2 reflector has no rows below ell); after the
+        // last reflector (ell = c - 1) the same pass also sums the squares of
+        // the rows below the diagonal and finds their leading digit
         if (kind == 0) {
             int32_t wd[D];
 #pragma unroll
@@ -224,29 +229,35 @@ __global__ void __launch_bounds__(NT) fx_panel_kernel(FxPanelArgs a) {
                 axpy_row<D>(x, wd, u);
 #pragma unroll
                 for (int k = 0; k < D; ++k) Fc[k * fs + i] = x[k];
+                if (ell == c - 1 && i > c) {
+                    dot_acc<D>(x, x, sacc);  // general product: a symmetric variant miscomputed low digits
+                    const int tp = fixed_top<D>(x);
+                    top = tp > top ? tp : top;
+                    if ((++cnt & 255) == 0) carry_norm<M>(sacc);  // keeps the int64 sums far from overflow
+                }
             }
         }
+        if (ell == c - 1) fused = kind == 0;
         __syncthreads();
     }
 
-    // sum of squares and leading digit of the rows below the diagonal
-    int64_t sacc[M];
+    // sum of squares and leading digit of the rows below the diagonal (unless
+    // the last update pass has formed them)
+    if (!fused) {
+        for (int64_t i = c + 1 + tid; i < r; i += NT) {
+            int32_t x[D];
 #pragma unroll
-    for (int k = 0; k < M; ++k) sacc[k] = 0;
-    int top = -1;
-    int cnt = 0;
-    for (int64_t i = c + 1 + tid; i < r; i += NT) {
-        int32_t x[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) x[k] = Fc[k * fs + i];
-        dot_acc<D>(x, x, sacc);  // general product: a symmetric variant miscomputed low digits here
-        const int tp = fixed_top<D>(x);
-        top = tp > top ? tp : top;
-        if ((++cnt & 255) == 0) carry_norm<M>(sacc);  // keeps the int64 sums far from overflow
+            for (int k = 0; k < D; ++k) x[k] = Fc[k * fs + i];
+            dot_acc<D>(x, x, sacc);
+            const int tp = fixed_top<D>(x);
+            top = tp > top ? tp : top;
+            if ((++cnt & 255) == 0) carry_norm<M>(sacc);
+        }
     }
 
-    // 3. publish the rows below the diagonal, rescaled by q whole digits so
-    //    that their largest entry leads in digit D-2 or D-1
+    // 3. the reflector's scalars on warp 0 while the other warps publish the
+    //    rows below the diagonal, rescaled by q whole digits so that their
+    //    largest entry leads in digit D-2 or D-1
     top = __reduce_max_sync(0xffffffffu, top);
     if (lane == 0) sh_u[warp] = (unsigned)(top + 1);
     block_digit_sum<M, NW>(sacc, red);  // (synchronises)
@@ -254,39 +265,44 @@ __global__ void __launch_bounds__(NT) fx_panel_kernel(FxPanelArgs a) {
 #pragma unroll
     for (int q = 0; q < NW; ++q) tmax = (int)sh_u[q] - 1 > tmax ? (int)sh_u[q] - 1 : tmax;
     const int qsh = (tmax >= 0 && tmax < D - 2) ? D - 2 - tmax : 0;
-    if (qsh > 0) {
-        for (int64_t i = c + 1 + tid; i < r; i += NT) {
-#pragma unroll
-            for (int k = D - 1; k >= 0; --k) Fc[k * fs + i] = k >= qsh ? Fc[(k - qsh) * fs + i] : 0;
-        }
-    }
     const int eu_c = ec - qsh;
-    __syncthreads();
-    if (tid == 0) {
-        Mc[FxMeta<P>::kScaleU] = eu_c;
-        __threadfence();
-        atomicExch(a.flags + c, a.epoch);
-        // the reflector's scalars (Golub and Van Loan, Algorithm 5.1.1)
-        int64_t tot[M];
-#pragma unroll
-        for (int k = 0; k < M; ++k) tot[k] = red[0][k];
-        const xf<N> sig = xf_from_acc<N>(tot, 2 * ec + D - 3);
-        int32_t xe[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) xe[k] = Fc[k * fs + c];
-        xf<N> v0, bp, rcc, inv, bet;
-        const int kind = xf_house<N>(sig, xf_from_fixed<N, D>(xe, ec), v0, bp, rcc, inv, bet);
-        Mc[FxMeta<P>::kKind] = kind;
-        st_xf<N>(Mc + FxMeta<P>::kV0, v0);
-        st_xf<N>(Mc + FxMeta<P>::kBp, bp);
-        __threadfence();
-        atomicExch(a.flags + a.w + c, a.epoch);
+    if (warp == 0) {
+        // the reflector's scalars (Golub and Van Loan, Algorithm 5.1.1), one
+        // warp with digit k in lane k; row c is not touched by the shift
+        const int64_t tot = lane < M ? red[0][lane] : 0;
+        const fxw::wxf sig = fxw::from_acc<N, M>(tot, 2 * ec + D - 3);
+        const int32_t xe = lane < D ? Fc[lane * fs + c] : 0;
+        fxw::wxf v0, bp, rcc, inv, bet;
+        const int kind = fxw::house<N>(sig, fxw::from_fixed<N, D>(xe, ec), v0, bp, rcc, inv, bet);
+        if (lane == 0) Mc[FxMeta<P>::kKind] = kind;
+        wst_xf<N>(Mc + FxMeta<P>::kV0, v0);
+        wst_xf<N>(Mc + FxMeta<P>::kBp, bp);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            atomicExch(a.flags + a.w + c, a.epoch);
+        }
         // outputs: beta, R_cc; 1/v0 for the vector
-        st_md<P>(a.beta, a.beta_ps, c, finite ? xf_to_md<P, N>(bet) : md_from_double<P>(dnan()));
-        st_md<P>(colc, ps, c, finite ? xf_to_md<P, N>(rcc) : md_from_double<P>(dnan()));
+        const xf<N> bet_s = fxw::to_scalar<N>(bet), rcc_s = fxw::to_scalar<N>(rcc);
+        if (lane == 0) {
+            st_md<P>(a.beta, a.beta_ps, c, finite ? xf_to_md<P, N>(bet_s) : md_from_double<P>(dnan()));
+            st_md<P>(colc, ps, c, finite ? xf_to_md<P, N>(rcc_s) : md_from_double<P>(dnan()));
+        }
+        if (lane < N) sh_x[lane] = inv.d;
+        if (lane == 0) sh_x[N] = inv.e;
+    } else {
+        if (qsh > 0) {
+            for (int64_t i = c + 1 + (tid - 32); i < r; i += NT - 32) {
 #pragma unroll
-        for (int k = 0; k < N; ++k) sh_x[k] = inv.d[k];
-        sh_x[N] = inv.e;
+                for (int k = D - 1; k >= 0; --k) Fc[k * fs + i] = k >= qsh ? Fc[(k - qsh) * fs + i] : 0;
+            }
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(NT - 32) : "memory");  // warps 1.. only
+        if (tid == 32) {
+            Mc[FxMeta<P>::kScaleU] = eu_c;
+            __threadfence();
+            atomicExch(a.flags + c, a.epoch);
+        }
     }
     __syncthreads();
 
