@@ -146,14 +146,14 @@ int tri_levels(int stage, cudaStream_t st, double* X, int64_t ldx, int64_t psx, 
                int64_t ntiles, int L) {
     StageScope sc(stage, st);
     for (int s = L; s < t; s *= 2) {
-        int KS = 1;
-        while (KS * 16 < s && KS < 4) KS *= 2;
-        const int nbs = (s + 7) / 8;
-        dim3 grid((unsigned)(nbs * nbs), (unsigned)((t + 2 * s - 1) / (2 * s)), (unsigned)ntiles);
-        const size_t smem = (size_t)KS * 64 * sizeof(md<P>);
-        tri_level_kernel<P, 0><<<grid, 64 * KS, smem, st>>>(X, ldx, psx, xtile, M, ldm, psm, mtile, n, t, s);
+        int KS = 1;  // k groups of at most 8 (16 for s = 128)
+        while (KS * 8 < s && KS < 8) KS *= 2;
+        const int nbi = (s + 7) / 8, nbj = (s + 3) / 4;
+        dim3 grid((unsigned)(nbi * nbj), (unsigned)((t + 2 * s - 1) / (2 * s)), (unsigned)ntiles);
+        const size_t smem = (size_t)KS * 32 * sizeof(md<P>);
+        tri_level_kernel<P, 0><<<grid, 32 * KS, smem, st>>>(X, ldx, psx, xtile, M, ldm, psm, mtile, n, t, s);
         MDLS_LAUNCH_CHECK();
-        tri_level_kernel<P, 1><<<grid, 64 * KS, smem, st>>>(X, ldx, psx, xtile, M, ldm, psm, mtile, n, t, s);
+        tri_level_kernel<P, 1><<<grid, 32 * KS, smem, st>>>(X, ldx, psx, xtile, M, ldm, psm, mtile, n, t, s);
         MDLS_LAUNCH_CHECK();
     }
     return MDLS_OK;
@@ -295,7 +295,8 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
         {
             const int L = w < kTriLeaf ? w : kTriLeaf;
             StageScope sc(ST_W, st);
-            wy_t_leaf_kernel<P><<<(unsigned)((w + 7) / 8), 128, 0, st>>>(G, t, tt2, beta, t, w, L, T, t, tt2);
+            // one warp (two rows) per block: the leaves spread over w/2 SMs
+            wy_t_leaf_kernel<P><<<(unsigned)((w + 1) / 2), 32, 0, st>>>(G, t, tt2, beta, t, w, L, T, t, tt2);
             MDLS_LAUNCH_CHECK();
             rc = tri_levels<P>(ST_W, st, T, t, tt2, 0, G, t, tt2, 0, w, w, 1, L);
             if (rc) return rc;

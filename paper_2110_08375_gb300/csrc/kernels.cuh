@@ -527,17 +527,19 @@ __global__ void wy_t_leaf_kernel(const double* G, int64_t ldg, int64_t psg, cons
 //   STEP 0: Z = M12 X2 (X2 upper triangular: k <= j), kept in the unused
 //           lower block of X as X[a+s+j, a+i] = Z(i, j);
 //   STEP 1: X12 = -X1 Z (X1 upper triangular: k >= i) into X[a+i, a+s+j].
-// An 8 x 8 output block per 64 threads; the k range is split over
-// blockDim.x / 64 (at most 4) groups whose partial sums meet in a fixed tree.
+// An 8 x 4 output block per warp (lanes along i: coalesced reads of M12 and
+// X1); the k range is split over blockDim.x / 32 (at most 8) warps whose
+// partial sums meet in a fixed tree.  Small blocks spread a level over most
+// SMs: each SM's shared FP64 unit, not the number of outputs, sets the pace.
 template <int P, int STEP>
 __global__ void __launch_bounds__(256) tri_level_kernel(double* X, int64_t ldx, int64_t psx, int64_t xtile, const double* M,
                                  int64_t ldm, int64_t psm, int64_t mtile, int64_t n, int t, int s) {
     extern __shared__ __align__(16) unsigned char tl_smem[];
     md<P>* red = reinterpret_cast<md<P>*>(tl_smem);
-    const int KS = blockDim.x >> 6;
-    const int tid = threadIdx.x & 63, kz = threadIdx.x >> 6;
-    const int nbs = (s + 7) >> 3;
-    const int i = (blockIdx.x % nbs) * 8 + (tid & 7), j = (blockIdx.x / nbs) * 8 + (tid >> 3);
+    const int KS = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, kz = threadIdx.x >> 5;
+    const int nbi = (s + 7) >> 3;
+    const int i = (blockIdx.x % nbi) * 8 + (lane & 7), j = (blockIdx.x / nbi) * 4 + (lane >> 3);
     const int64_t b = blockIdx.z;
     const int64_t a = (int64_t)blockIdx.y * 2 * s;
     const int64_t tt = (n - b * t) < t ? (n - b * t) : t;
@@ -563,15 +565,15 @@ __global__ void __launch_bounds__(256) tri_level_kernel(double* X, int64_t ldx, 
                                 ld_md<P>(Xb, psx, (a + k) * ldx + a + s + j));
         }
     }
-    red[kz * 64 + tid] = acc;
+    red[kz * 32 + lane] = acc;
     __syncthreads();
     for (int hh = KS / 2; hh > 0; hh >>= 1) {
-        if (kz < hh) red[kz * 64 + tid] = md_add<P>(red[kz * 64 + tid], red[(kz + hh) * 64 + tid]);
+        if (kz < hh) red[kz * 32 + lane] = md_add<P>(red[kz * 32 + lane], red[(kz + hh) * 32 + lane]);
         __syncthreads();
     }
     if (kz != 0 || !out) return;
-    if (STEP == 0) st_md<P>(Xb, psx, (a + i) * ldx + a + s + j, red[tid]);
-    else st_md<P>(Xb, psx, (a + s + j) * ldx + a + i, md_neg<P>(red[tid]));
+    if (STEP == 0) st_md<P>(Xb, psx, (a + i) * ldx + a + s + j, red[lane]);
+    else st_md<P>(Xb, psx, (a + s + j) * ldx + a + i, md_neg<P>(red[lane]));
 }
 
 // Elementwise md arithmetic (mdls_vec_op).
