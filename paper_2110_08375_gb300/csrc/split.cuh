@@ -128,11 +128,14 @@ DEV_INLINE void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], const uint
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Shared memory: the digit slices staged per k16 step, reused after the k
+// loop for the S diagonal sums of the epilogue (two blocks per SM fit).
 template <int P>
 constexpr size_t split_gemm_smem() {
     constexpr int S = SplitCfg<P>::S;
-    return (size_t)S * kSplitTm * kSplitPad * 2 + (size_t)S * kSplitTn * kSplitPad * 2 +
-           (size_t)S * kSplitTm * kSplitTn * 8;
+    constexpr size_t stage = (size_t)S * kSplitTm * kSplitPad * 2 + (size_t)S * kSplitTn * kSplitPad * 2;
+    constexpr size_t diag = (size_t)S * kSplitTm * kSplitTn * 8;
+    return stage > diag ? stage : diag;
 }
 
 // C(i,j) = [C] +/- 2^(ea_i + fb_j) sum_q D_q(i,j) 256^-(q+2), one 16x8 tile
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(256)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __nv_bfloat16* Asm = reinterpret_cast<__nv_bfloat16*>(smem_raw);             // [S][16][24]
     __nv_bfloat16* Bsm = Asm + (size_t)S * kSplitTm * kSplitPad;                  // [S][8][24]
-    long long* Dsm = reinterpret_cast<long long*>(Bsm + (size_t)S * kSplitTn * kSplitPad);  // [S][128]
+    long long* Dsm = reinterpret_cast<long long*>(smem_raw);  // [S][128], after the k loop
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t4 = lane & 3;
     const int64_t i0 = (int64_t)blockIdx.x * kSplitTm, j0 = (int64_t)blockIdx.y * kSplitTn;

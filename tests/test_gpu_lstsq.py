@@ -76,3 +76,17 @@ def test_workspace_reuse_gives_identical_results():
     ws = mdls.mdls_lstsq(Ad, bd, x1, tile=16)
     mdls.mdls_lstsq(Ad, bd, x2, tile=16, ws=ws)
     assert torch.equal(x1, x2)
+
+
+@pytest.mark.parametrize("p", [2, 4, 8])
+def test_lstsq_widest_tile(p):
+    """Tile 256, the widest the ABI accepts: the panel's 256 column blocks must
+    all be resident at once (cooperative launch), in every precision."""
+    import torch
+    import paper_2110_08375_gb300 as mdls
+    m, n = 300, 260
+    A, b = synth.lstsq_problem(p, m, n, seed=9, tag="wide")
+    xd = torch.zeros((p, n), dtype=torch.float64, device="cuda")
+    ws = mdls.mdls_lstsq(to_dev(A), to_dev(b), xd, tile=256)
+    assert mdls.mdls_read_status(ws) == 0
+    assert oracle.rel_err(to_host(xd), oracle.lstsq(A, b)) < TOL[p]
