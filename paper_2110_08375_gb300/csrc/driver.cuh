@@ -16,9 +16,10 @@ constexpr int panel_threads() {
     return P == 8 ? 128 : 256;
 }
 
-// Integer-digit panel: threads per column.  Octo double keeps 128 (about 170
-// registers each): at 256 threads one block per SM would cap the tile at the
-// SM count.
+// Integer-digit panel: threads per column.  The kernel is built for two
+// blocks per SM (all w column blocks of a tile up to 256 wide must be
+// resident at once); octo double needs more than 128 registers per thread
+// and keeps 128 threads.
 template <int P>
 constexpr int fx_panel_threads() {
     return P == 8 ? 128 : 256;

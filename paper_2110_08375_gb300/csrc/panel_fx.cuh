@@ -85,7 +85,7 @@ DEV_INLINE void block_digit_sum(int64_t (&acc)[M], int64_t (*red)[M]) {
 }
 
 template <int P, int NT>
-__global__ void __launch_bounds__(NT) fx_panel_kernel(FxPanelArgs a) {
+__global__ void __launch_bounds__(NT, 2) fx_panel_kernel(FxPanelArgs a) {
     using namespace fx;
     constexpr int D = Cfg<P>::D, N = Cfg<P>::N, NW = NT / 32, MI = FxMeta<P>::ints;
     constexpr int M = D + 3;  // digit diagonals of a dot product
