@@ -5,8 +5,8 @@
 // caller's), captures every problem's launch sequence into one graph -- the
 // problems spread over parallel branches, largest first, each branch fed the
 // next problem when it has the least estimated work -- and instantiates it.
-// Each problem uses the single-block panel, so no problem ever waits on
-// blocks of its own that the others keep off the SMs.  mdls_batched_launch()
+// Each problem uses the single-block panel (integer digits, one block), so
+// no problem ever waits on blocks of its own that the others keep off the SMs.  mdls_batched_launch()
 // replays the graph on a stream.
 //
 // Autotuner: for every (precision, n-bucket) class not seen before (n
@@ -58,10 +58,10 @@ bool problem_ok(const mdls_problem& p) {
 
 size_t problem_ws(const mdls_problem& p) {
     size_t best = 0;
-    if (p.tile > 0) return align256(ls_layout(p.prec, p.m, p.n, norm_tile(p.tile, p.n), false, false).total);
+    if (p.tile > 0) return align256(ls_layout(p.prec, p.m, p.n, norm_tile(p.tile, p.n)).total);
     for (int c : kCandidates) {
         const int t = norm_tile(c, p.n);
-        best = std::max(best, ls_layout(p.prec, p.m, p.n, t, false, false).total);
+        best = std::max(best, ls_layout(p.prec, p.m, p.n, t).total);
     }
     return align256(best);
 }

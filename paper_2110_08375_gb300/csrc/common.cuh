@@ -97,65 +97,19 @@ struct ViewUpperT {
 };
 
 // ----------------------------------------------------------------------------
-// Workspace header: status word and grid-barrier state live at the start of
-// every workspace the caller hands in.
+// Workspace header: the status word and the failure flag of the bounded waits
+// live at the start of every workspace the caller hands in.
 // ----------------------------------------------------------------------------
 struct WsHeader {
     int status;            // first error seen on the device (0 = none)
     int pad0;
-    unsigned int bar_count;  // grid barrier: arrivals of the current generation
-    unsigned int bar_gen;    // grid barrier: generation
+    unsigned int reserved0;
+    unsigned int reserved1;
     int bar_error;           // set by a bounded wait that gave up: later waits fail fast
     int pad2[59];            // header is 256 bytes
 };
 static_assert(sizeof(WsHeader) == 256, "workspace header must be 256 bytes");
 
 DEV_INLINE void set_status(int* status, int code) { atomicCAS(status, 0, code); }
-
-// Grid-wide barrier of a cooperative launch (all blocks co-resident).  Every
-// wait is bounded: after about kBarrierTimeoutCycles the waiting block raises
-// bar_error and MDLS_ERR_TIMEOUT and returns false; once bar_error is set all
-// later barriers return false at once, so every block leaves the kernel in
-// bounded time.  A single block needs no barrier.
-constexpr long long kBarrierTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
-
-__device__ __forceinline__ bool grid_barrier(WsHeader* h) {
-    __syncthreads();
-    if (gridDim.x == 1) return true;
-    __shared__ int ok_s;
-    if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &h->bar_gen;
-        volatile int* verr = &h->bar_error;
-        int ok = (*verr == 0);
-        if (ok) {
-            const unsigned int g = *vgen;
-            __threadfence();
-            const unsigned int arrived = atomicAdd(&h->bar_count, 1u);
-            if (arrived == gridDim.x - 1) {
-                h->bar_count = 0;
-                __threadfence();
-                atomicAdd(&h->bar_gen, 1u);
-            } else {
-                const long long t0 = clock64();
-                while (*vgen == g) {
-                    if (*verr) { ok = 0; break; }
-                    if (clock64() - t0 > kBarrierTimeoutCycles) {
-                        atomicExch(&h->bar_error, 1);
-                        set_status(&h->status, MDLS_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            __threadfence();
-        }
-        ok_s = ok;
-    }
-    __syncthreads();
-    const int ok = ok_s;
-    __syncthreads();
-    return ok != 0;
-}
 
 }  // namespace mdls

@@ -11,17 +11,18 @@
 
 namespace mdls {
 
-template <int P>
-constexpr int panel_threads() {
-    return P == 8 ? 128 : 256;
-}
-
 // Integer-digit panel: threads per column.  The kernel is built for two
 // blocks per SM (all w column blocks of a tile up to 256 wide must be
 // resident at once); octo double needs more than 128 registers per thread
 // and keeps 128 threads.
 template <int P>
 constexpr int fx_panel_threads() {
+    return P == 8 ? 128 : 256;
+}
+
+// Single-block digit panel (batched problems): threads of its one block.
+template <int P>
+constexpr int fx_block_threads() {
     return P == 8 ? 128 : 256;
 }
 
@@ -233,7 +234,6 @@ template <int P>
 int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa, double* Q,
            int64_t ldq, int64_t psq, int t, char* ws, const QrLayout& L, WsHeader* hdr,
            bool zero_lower, cudaStream_t st, bool keep_w = false, bool single_block = false) {
-    constexpr int NT = panel_threads<P>();
     static_assert(fx_digits(P) == fx::Cfg<P>::D && fx_meta_ints(P) == FxMeta<P>::ints,
                   "host and device digit layouts differ");
     double* beta = reinterpret_cast<double*>(ws + L.beta);
@@ -244,9 +244,6 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
     unsigned int* flags = reinterpret_cast<unsigned int*>(ws + L.flags);
     int32_t* fxF = reinterpret_cast<int32_t*>(ws + L.fxF);
     int32_t* fxmeta = reinterpret_cast<int32_t*>(ws + L.fxmeta);
-    double* part = reinterpret_cast<double*>(ws + L.part);
-    double* wvec = reinterpret_cast<double*>(ws + L.wvec);
-    const int64_t part_ps = (int64_t)kMaxPanelBlocks * (t + 1);
     TcBuf tcb{};
     if (L.tc_as_cap > 0) {
         tcb = TcBuf{reinterpret_cast<__nv_bfloat16*>(ws + L.tc_as), reinterpret_cast<__nv_bfloat16*>(ws + L.tc_bs),
@@ -272,8 +269,8 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
         {
             StageScope sc(ST_PANEL, st);
             if (single_block) {
-                RowPanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, part, part_ps, wvec, hdr};
-                panel_rows_kernel<P, NT><<<1, NT, 0, st>>>(pa);
+                FxBlockPanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, fxF, hdr};
+                fx_panel_block_kernel<P, fx_block_threads<P>()><<<1, fx_block_threads<P>(), 0, st>>>(pa);
                 MDLS_LAUNCH_CHECK();
             } else {
                 if (w > panel_capacity<P>()) return MDLS_ERR_UNSUPPORTED;
@@ -506,7 +503,7 @@ template <int P>
 int ls_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa, const double* b,
              int64_t psb, double* x, int64_t psx, int t, int mode, void* ws, cudaStream_t st,
              bool single_block = false) {
-    LsLayout L = ls_layout(P, m, n, t, mode == MDLS_MODE_SPLIT, !single_block);
+    LsLayout L = ls_layout(P, m, n, t, mode == MDLS_MODE_SPLIT);
     char* w = static_cast<char*>(ws);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(w);
     if (cudaMemsetAsync(w, 0, L.qr.flags + L.qr.flag_bytes, st) != cudaSuccess) return MDLS_ERR_CUDA;

@@ -10,31 +10,6 @@ DEV_INLINE md<P> md_one() {
     return md_from_double<P>(1.0);
 }
 
-// loads that bypass L1 (data written by other blocks of the same launch)
-template <int P>
-DEV_INLINE md<P> ld_md_cg(const double* ptr, int64_t ps, int64_t off) {
-    md<P> r;
-#pragma unroll
-    for (int l = 0; l < P; ++l) r.v[l] = __ldcg(ptr + l * ps + off);
-    return r;
-}
-
-// Deterministic block reduction (fixed binary tree), result in every thread.
-template <int P, int NT>
-DEV_INLINE md<P> block_sum(md<P> x, md<P>* red) {
-    const int tid = threadIdx.x;
-    red[tid] = x;
-    __syncthreads();
-#pragma unroll 1
-    for (int s = NT / 2; s > 0; s >>= 1) {
-        if (tid < s) red[tid] = md_add<P>(red[tid], red[tid + s]);
-        __syncthreads();
-    }
-    md<P> r = red[0];
-    __syncthreads();
-    return r;
-}
-
 // Deterministic warp reduction: a fixed shfl_down tree ending in lane 0,
 // whose sum is then broadcast, so every lane gets the same bits.
 template <int P>
@@ -85,32 +60,6 @@ DEV_INLINE md<P> md_select(bool c, const md<P>& a, const md<P>& b) {
 
 constexpr long long kFlagTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
 
-// Householder scalars of x = (x0, x_1..): sigma = sum_{i>0} x_i^2 given.
-// kind 0: general (beta, 1/v0, R = mu), 1: identity (beta = 0, R = x0),
-// 2: reflect e1 (beta = 2, R = -x0); Golub & Van Loan Alg. 5.1.1.
-template <int P>
-DEV_INLINE void house_scalars(const md<P>& sig, const md<P>& x0, md<P>& beta, md<P>& inv, md<P>& rcc,
-                              int& kind) {
-    if (sig.v[0] == 0.0) {
-        inv = md_zero<P>();
-        if (x0.v[0] >= 0.0) {
-            kind = 1; beta = md_zero<P>(); rcc = x0;
-        } else {
-            kind = 2; beta = md_from_double<P>(2.0); rcc = md_neg<P>(x0);
-        }
-        return;
-    }
-    kind = 0;
-    const md<P> mu = md_sqrt<P>(md_fma<P>(sig, x0, x0));
-    md<P> v0;
-    if (x0.v[0] <= 0.0) v0 = md_sub<P>(x0, mu);
-    else v0 = md_neg<P>(md_div<P>(sig, md_add<P>(x0, mu)));  // -sigma/(x0+mu)
-    // beta = 2 v0^2 / (sigma + v0^2) = -v0 / mu, since sigma + v0^2 = -2 mu v0
-    beta = md_neg<P>(md_div<P>(v0, mu));
-    inv = md_div<P>(md_one<P>(), v0);
-    rcc = mu;
-}
-
 // Waits (thread 0 only) until *flag == want.  Bounded: on timeout it records
 // MDLS_ERR_TIMEOUT and returns false.  Also returns false when another block
 // has already failed.
@@ -129,128 +78,6 @@ DEV_INLINE bool wait_flag(const unsigned int* flag, unsigned int want, WsHeader*
     }
     __threadfence();
     return true;
-}
-
-// ----------------------------------------------------------------------------
-// Row-split panel: step 1 of Algorithm 2 with every block sharing every
-// column (used with a single block for the small problems of batched solves,
-// where a panel must not wait on blocks of its own that other work keeps off
-// the SMs).  Block b owns rows [b*rows_per, ...) of the panel (all w columns).
-// Per column l: (1) partial sigma over my rows -> grid barrier -> every block
-// sums the partials (fixed tree) and computes the reflector's scalars
-// ("beta, v"); (2) my rows of v, partial v^T a_c for every column c > l ->
-// barrier -> block b sums the partials of column l+1+b (fixed tree), forms
-// w_c = beta v^T a_c and publishes it ("beta R^T v") -> barrier; (3) my rows
-// of every column c > l get a_c -= v w_c ("update R").  The owner of row l
-// writes R_ll.  With one block (small problems) there is no barrier at all.
-// Scratch: part (gridDim.x x (w+1) md), wvec (w md).
-// ----------------------------------------------------------------------------
-struct RowPanelArgs {
-    double* A;
-    int64_t ld, ps;
-    int64_t j0, r;
-    int w;
-    double* beta;
-    int64_t beta_ps;
-    double* part;     // [b][c] partials: part + (b*(w+1) + c); plane stride part_ps
-    int64_t part_ps;
-    double* wvec;     // w_c; plane stride w
-    WsHeader* hdr;
-};
-
-template <int P, int NT>
-__global__ void __launch_bounds__(NT) panel_rows_kernel(RowPanelArgs a) {
-    const int tid = threadIdx.x, nb = gridDim.x, b = blockIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    constexpr int NW = NT / 32;
-    const int64_t ld = a.ld, ps = a.ps;
-    double* base = a.A + a.j0 * ld + a.j0;
-    const int64_t rows_per = (a.r + nb - 1) / nb;
-    const int64_t rb0 = (int64_t)b * rows_per;
-    const int64_t rb1 = (rb0 + rows_per) < a.r ? (rb0 + rows_per) : a.r;
-    const int W1 = a.w + 1;
-    __shared__ md<P> red[NT];
-    __shared__ md<P> sh_scal[3];
-    __shared__ int sh_kind;
-    for (int ell = 0; ell < a.w; ++ell) {
-        double* col = base + (int64_t)ell * ld;
-        // (1) sigma
-        md<P> sig = md_zero<P>();
-        for (int64_t i = (rb0 > ell + 1 ? rb0 : ell + 1) + tid; i < rb1; i += NT) {
-            const md<P> xi = ld_md<P>(col, ps, i);
-            sig = md_fma<P>(sig, xi, xi);
-        }
-        sig = block_sum<P, NT>(sig, red);
-        if (nb > 1) {
-            if (tid == 0) st_md<P>(a.part, a.part_ps, (int64_t)b * W1 + a.w, sig);
-            if (!grid_barrier(a.hdr)) return;
-            md<P> s = md_zero<P>();
-            for (int q = tid; q < nb; q += NT) s = md_add<P>(s, ld_md_cg<P>(a.part, a.part_ps, (int64_t)q * W1 + a.w));
-            sig = block_sum<P, NT>(s, red);
-        }
-        if (tid == 0) {
-            md<P> beta, inv, rcc;
-            int kind;
-            house_scalars<P>(sig, ld_md_cg<P>(col, ps, ell), beta, inv, rcc, kind);
-            sh_scal[0] = beta;
-            sh_scal[1] = inv;
-            sh_scal[2] = rcc;
-            sh_kind = kind;
-        }
-        __syncthreads();
-        const int kind = sh_kind;
-        const md<P> beta = sh_scal[0];
-        if (kind == 0) {
-            const md<P> inv = sh_scal[1];
-            for (int64_t i = (rb0 > ell + 1 ? rb0 : ell + 1) + tid; i < rb1; i += NT)
-                st_md<P>(col, ps, i, md_mul<P>(ld_md<P>(col, ps, i), inv));
-        }
-        __syncthreads();
-        // (2) partial dots v^T a_c over my rows (one warp per column, lanes over rows)
-        const int64_t lo = rb0 > ell ? rb0 : ell;
-        if (kind != 1) {
-            for (int c = ell + 1 + warp; c < a.w; c += NW) {
-                const double* cc = base + (int64_t)c * ld;
-                md<P> s = md_zero<P>();
-                for (int64_t i = lo + lane; i < rb1; i += 32) {
-                    const md<P> vi = (i == ell) ? md_one<P>() : ld_md<P>(col, ps, i);
-                    s = md_fma<P>(s, vi, ld_md<P>(cc, ps, i));
-                }
-                s = warp_sum<P>(s);
-                if (lane == 0) {
-                    if (nb > 1) st_md<P>(a.part, a.part_ps, (int64_t)b * W1 + c, s);
-                    else st_md<P>(a.wvec, a.w, c, md_mul<P>(beta, s));
-                }
-            }
-        }
-        if (nb > 1) {
-            if (!grid_barrier(a.hdr)) return;
-            // block b reduces the partials of columns c = ell+1+b, ell+1+b+nb, ...
-            for (int c = ell + 1 + b; c < a.w && kind != 1; c += nb) {
-                md<P> s = md_zero<P>();
-                for (int q = tid; q < nb; q += NT) s = md_add<P>(s, ld_md_cg<P>(a.part, a.part_ps, (int64_t)q * W1 + c));
-                s = block_sum<P, NT>(s, red);
-                if (tid == 0) st_md<P>(a.wvec, a.w, c, md_mul<P>(beta, s));
-            }
-            if (!grid_barrier(a.hdr)) return;
-        } else {
-            __syncthreads();
-        }
-        // (3) update my rows of the trailing panel columns
-        if (kind != 1) {
-            for (int c = ell + 1 + warp; c < a.w; c += NW) {
-                double* cc = base + (int64_t)c * ld;
-                const md<P> wc = nb > 1 ? ld_md_cg<P>(a.wvec, a.w, c) : ld_md<P>(a.wvec, a.w, c);
-                for (int64_t i = lo + lane; i < rb1; i += 32) {
-                    const md<P> vi = (i == ell) ? md_one<P>() : ld_md<P>(col, ps, i);
-                    st_md<P>(cc, ps, i, md_fms<P>(ld_md<P>(cc, ps, i), vi, wc));
-                }
-            }
-        }
-        if (tid == 0 && ell >= rb0 && ell < rb1) st_md<P>(col, ps, ell, sh_scal[2]);
-        if (tid == 0 && b == 0) st_md<P>(a.beta, a.beta_ps, ell, beta);
-        __syncthreads();
-    }
 }
 
 // ----------------------------------------------------------------------------

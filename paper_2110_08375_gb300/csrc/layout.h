@@ -18,7 +18,6 @@ struct Bump {
     }
 };
 
-constexpr int kMaxPanelBlocks = 512;
 
 // Integer-digit panel: 24-bit digits per entry for P limbs (53P bits plus 64
 // of guard and headroom) and the ints of a column's published record; the
@@ -27,7 +26,7 @@ constexpr int fx_digits(int P) { return (53 * P + 64 + 23) / 24; }
 constexpr int fx_meta_ints(int P) { return 4 + 2 * (fx_digits(P) + 1); }
 
 struct QrLayout {
-    size_t flags, flag_bytes, beta, fxF, fxmeta, G, T, X, W, split, part, wvec;
+    size_t flags, flag_bytes, beta, fxF, fxmeta, G, T, X, W, split;
     int64_t xcols, wcols, split_cap;
     // tensor-core digit slices (split mode; caps 0 otherwise)
     size_t tc_as, tc_bs, tc_ea, tc_fb, tc_as_cap, tc_bs_cap;
@@ -49,16 +48,14 @@ struct LsLayout {
 };
 
 inline QrLayout qr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool want_q, int nextra,
-                             bool keep_w = false, bool split = false, bool fx_panel = true) {
+                             bool keep_w = false, bool split = false) {
     QrLayout L;
     L.flag_bytes = align256(2 * (size_t)t * sizeof(unsigned int));
     L.flags = B.take(L.flag_bytes);
     const size_t d = sizeof(double) * (size_t)P;
-    L.part = B.take(d * (size_t)kMaxPanelBlocks * (size_t)(t + 1));  // panel partial sums
-    L.wvec = B.take(d * (size_t)t);
     L.beta = B.take(d * t);
     // integer-digit panel: the panel's digits and each column's record
-    L.fxF = fx_panel ? B.take(4 * (size_t)fx_digits(P) * (size_t)t * (size_t)m) : 0;
+    L.fxF = B.take(4 * (size_t)fx_digits(P) * (size_t)t * (size_t)m);
     L.fxmeta = B.take(4 * (size_t)fx_meta_ints(P) * (size_t)t);
     L.G = B.take(d * t * t);
     L.T = B.take(d * t * t);
@@ -146,10 +143,10 @@ inline RefLayout ref_layout(int P, int64_t m, int64_t n, int t) {
     return L;
 }
 
-inline LsLayout ls_layout(int P, int64_t m, int64_t n, int t, bool split = false, bool fx_panel = true) {
+inline LsLayout ls_layout(int P, int64_t m, int64_t n, int t, bool split = false) {
     Bump B;
     LsLayout L;
-    L.qr = qr_layout_at(B, P, m, n, t, false, 1, false, split, fx_panel);
+    L.qr = qr_layout_at(B, P, m, n, t, false, 1, false, split);
     L.Aw = B.take(sizeof(double) * (size_t)P * (size_t)m * (size_t)(n + 1));
     L.bs = bs_layout_at(B, P, n, t);
     L.total = B.off;

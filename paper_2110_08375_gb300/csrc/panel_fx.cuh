@@ -324,4 +324,251 @@ __global__ void __launch_bounds__(NT, 2) fx_panel_kernel(FxPanelArgs a) {
     }
 }
 
+// ----------------------------------------------------------------------------
+// The same panel in ONE block, for the small problems of batched solves: a
+// panel must not wait on blocks of its own that concurrent work keeps off the
+// SMs, so the column chain runs inside the block (right-looking, unblocked
+// Householder over the w columns) with the arithmetic of fx_panel_kernel:
+// each column in 24-bit digits at the scale set by its norm, dot products and
+// updates exact by digit diagonals, the reflector's scalars on warp 0, and
+// for each later column j one warp forms u . a_j, that column's
+// w = bp (v0 a_j[c] + u . a_j) and the update a_j -= w u.  The vectors and
+// R are written back to multiple doubles once, after the last column.
+// Scratch: F (digits, as in fx_panel_kernel); the per-column scales and
+// 1/v0 live in shared memory (w <= 256).
+// ----------------------------------------------------------------------------
+struct FxBlockPanelArgs {
+    double* A;
+    int64_t ld, ps;
+    int64_t j0;
+    int64_t r;
+    int w;
+    double* beta;
+    int64_t beta_ps;
+    int32_t* F;
+    WsHeader* hdr;
+};
+
+constexpr int kFxBlockMaxW = 256;
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) fx_panel_block_kernel(FxBlockPanelArgs a) {
+    using namespace fx;
+    constexpr int D = Cfg<P>::D, N = Cfg<P>::N, NW = NT / 32;
+    constexpr int M = D + 3;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t r = a.r, ps = a.ps, fs = (int64_t)a.w * r;
+    const int w = a.w;
+    double* base = a.A + a.j0 * a.ld + a.j0;
+
+    __shared__ int64_t red[NW][M];
+    __shared__ int sh_ec[kFxBlockMaxW], sh_eu[kFxBlockMaxW], sh_kind[kFxBlockMaxW];
+    __shared__ unsigned char sh_fin[kFxBlockMaxW];
+    __shared__ int32_t sh_inv[kFxBlockMaxW][N + 1];
+    __shared__ int32_t sh_v0[N + 1], sh_bp[N + 1];
+    __shared__ double sh_d[NW];
+    __shared__ unsigned sh_u[NW];
+
+    // 0. every column in digits at the scale of its norm (see fx_panel_kernel)
+    for (int c = 0; c < w; ++c) {
+        const double* colc = base + (int64_t)c * a.ld;
+        unsigned hmax = 0;
+        for (int64_t i = tid; i < r; i += NT) {
+#pragma unroll
+            for (int l = 0; l < P; ++l) {
+                const unsigned h = (unsigned)(dbits(colc[l * ps + i]) >> 32) & 0x7fffffffu;
+                hmax = h > hmax ? h : hmax;
+            }
+        }
+        hmax = __reduce_max_sync(0xffffffffu, hmax);
+        if (lane == 0) sh_u[warp] = hmax;
+        __syncthreads();
+        hmax = 0;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) hmax = sh_u[q] > hmax ? sh_u[q] : hmax;
+        const bool finite = hmax < 0x7ff00000u;
+        int emax = (int)(hmax >> 20) - 1023;
+        if (emax < -1022) emax = -1022;
+        if (emax > 1000) emax = 1000;
+        const double down = dfrom((uint64_t)(1023 - emax) << 52);
+        double ss = 0.0;
+        if (finite)
+            for (int64_t i = tid; i < r; i += NT) {
+                const double v = colc[i] * down;
+                ss = __fma_rn(v, v, ss);
+            }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, off);
+        if (lane == 0) sh_d[warp] = ss;
+        __syncthreads();
+        ss = 0.0;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) ss += sh_d[q];
+        int ec = -D;
+        if (finite && ss > 0.0) {
+            int k;
+            frexp(sqrt(ss), &k);
+            const int bound = emax + k + 1;
+            ec = floordiv24(bound + 3 + kB - 1) - D;
+        }
+        int32_t* Fc = a.F + (int64_t)c * r;
+        for (int64_t i = tid; i < r; i += NT) {
+            int32_t d[D];
+            if (finite) {
+                fixed_from_md<P, D>(ld_md<P>(colc, ps, i), ec, d);
+            } else {
+#pragma unroll
+                for (int k = 0; k < D; ++k) d[k] = 0;
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k) Fc[k * fs + i] = d[k];
+        }
+        if (tid == 0) {
+            sh_ec[c] = ec;
+            sh_fin[c] = finite ? 1 : 0;
+        }
+        __syncthreads();
+    }
+
+    for (int c = 0; c < w; ++c) {
+        const int ec = sh_ec[c];
+        int32_t* Fc = a.F + (int64_t)c * r;
+        // 1. sum of squares and leading digit of the rows below the diagonal
+        int64_t sacc[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) sacc[k] = 0;
+        int top = -1, cnt = 0;
+        for (int64_t i = c + 1 + tid; i < r; i += NT) {
+            int32_t x[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) x[k] = Fc[k * fs + i];
+            dot_acc<D>(x, x, sacc);
+            const int tp = fixed_top<D>(x);
+            top = tp > top ? tp : top;
+            if ((++cnt & 255) == 0) carry_norm<M>(sacc);
+        }
+        top = __reduce_max_sync(0xffffffffu, top);
+        if (lane == 0) sh_u[warp] = (unsigned)(top + 1);
+        block_digit_sum<M, NW>(sacc, red);  // (synchronises)
+        int tmax = -1;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) tmax = (int)sh_u[q] - 1 > tmax ? (int)sh_u[q] - 1 : tmax;
+        const int qsh = (tmax >= 0 && tmax < D - 2) ? D - 2 - tmax : 0;
+        const int eu = ec - qsh;
+        // 2. the reflector's scalars on warp 0; the other warps rescale the
+        //    rows below the diagonal by qsh whole digits (row c is untouched)
+        if (warp == 0) {
+            const int64_t tot = lane < M ? red[0][lane] : 0;
+            const fxw::wxf sig = fxw::from_acc<N, M>(tot, 2 * ec + D - 3);
+            const int32_t xe = lane < D ? Fc[lane * fs + c] : 0;
+            fxw::wxf v0, bp, rcc, inv, bet;
+            const int kind = fxw::house<N>(sig, fxw::from_fixed<N, D>(xe, ec), v0, bp, rcc, inv, bet);
+            if (lane < N) {
+                sh_v0[lane] = v0.d;
+                sh_bp[lane] = bp.d;
+                sh_inv[c][lane] = inv.d;
+            }
+            if (lane == 0) {
+                sh_v0[N] = v0.e;
+                sh_bp[N] = bp.e;
+                sh_inv[c][N] = inv.e;
+                sh_kind[c] = kind;
+                sh_eu[c] = eu;
+            }
+            const xf<N> bet_s = fxw::to_scalar<N>(bet), rcc_s = fxw::to_scalar<N>(rcc);
+            if (lane == 0) {
+                const bool fin = sh_fin[c] != 0;
+                st_md<P>(a.beta, a.beta_ps, c, fin ? xf_to_md<P, N>(bet_s) : md_from_double<P>(dnan()));
+                st_md<P>(base + (int64_t)c * a.ld, ps, c, fin ? xf_to_md<P, N>(rcc_s) : md_from_double<P>(dnan()));
+            }
+        } else if (qsh > 0) {
+            for (int64_t i = c + 1 + (tid - 32); i < r; i += NT - 32) {
+#pragma unroll
+                for (int k = D - 1; k >= 0; --k) Fc[k * fs + i] = k >= qsh ? Fc[(k - qsh) * fs + i] : 0;
+            }
+        }
+        __syncthreads();
+        // 3. columns j > c, one warp each: u . a_j over the rows below c, the
+        //    scalars w = bp (v0 a_j[c] + u . a_j), a_j[c] -= w v0, a_j -= w u
+        const int kind = sh_kind[c];
+        for (int j = c + 1 + warp; j < w; j += NW) {
+            const int ecj = sh_ec[j];
+            int32_t* Fj = a.F + (int64_t)j * r;
+            int64_t acc[M];
+#pragma unroll
+            for (int k = 0; k < M; ++k) acc[k] = 0;
+            int cj = 0;
+            for (int64_t i = c + 1 + lane; i < r; i += 32) {
+                int32_t u[D], x[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    u[k] = Fc[k * fs + i];
+                    x[k] = Fj[k * fs + i];
+                }
+                dot_acc<D>(u, x, acc);
+                if ((++cj & 255) == 0) carry_norm<M>(acc);
+            }
+            carry_norm<M>(acc);  // digits below 2^24: 32 of them sum in an int
+            int64_t mine = 0;
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const int sk = __reduce_add_sync(0xffffffffu, (int)acc[k]);
+                if (lane == k) mine = sk;
+            }
+            const fxw::wxf v0{lane < N ? sh_v0[lane] : 0, sh_v0[N]};
+            const fxw::wxf bp{lane < N ? sh_bp[lane] : 0, sh_bp[N]};
+            const int32_t xe = lane < D ? Fj[lane * fs + c] : 0;
+            const fxw::wxf x_c = fxw::from_fixed<N, D>(xe, ecj);
+            const fxw::wxf sv = fxw::add<N>(fxw::from_acc<N, M>(mine, eu + ecj + D - 3), fxw::mul<N>(v0, x_c));
+            const fxw::wxf W = fxw::mul<N>(bp, sv);
+            int32_t xn;
+            bool ok = fxw::fixed_from_xf<N, D>(fxw::sub<N>(x_c, fxw::mul<N>(W, v0)), ecj, xn);
+            if (lane < D) Fj[lane * fs + c] = xn;
+            int32_t wdk = 0;
+            if (kind == 0) ok = fxw::fixed_from_xf<N, D>(W, ecj - eu - (D - 2), wdk) && ok;
+            if (!ok && lane == 0) set_status(&a.hdr->status, MDLS_ERR_UNSUPPORTED);
+            if (kind == 0) {
+                int32_t wd[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) wd[k] = __shfl_sync(0xffffffffu, wdk, k);
+                for (int64_t i = c + 1 + lane; i < r; i += 32) {
+                    int32_t u[D], x[D];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        u[k] = Fc[k * fs + i];
+                        x[k] = Fj[k * fs + i];
+                    }
+                    axpy_row<D>(x, wd, u);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) Fj[k * fs + i] = x[k];
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // 4. write back every column: R above the diagonal, v = u / v0 below it
+    for (int c = 0; c < w; ++c) {
+        double* colc = base + (int64_t)c * a.ld;
+        const int32_t* Fc = a.F + (int64_t)c * r;
+        const bool fin = sh_fin[c] != 0;
+        const int ec = sh_ec[c], eu = sh_eu[c];
+        xf<N> inv;
+#pragma unroll
+        for (int k = 0; k < N; ++k) inv.d[k] = sh_inv[c][k];
+        inv.e = sh_inv[c][N];
+        for (int64_t i = tid; i < r; i += NT) {
+            if (i == c) continue;
+            int32_t x[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) x[k] = Fc[k * fs + i];
+            md<P> y;
+            if (!fin) y = md_from_double<P>(dnan());
+            else if (i < c) y = xf_to_md<P, N>(xf_from_fixed<N, D>(x, ec));
+            else y = xf_to_md<P, N>(xf_mul<N>(xf_from_fixed<N, D>(x, eu), inv));
+            st_md<P>(colc, ps, i, y);
+        }
+    }
+}
+
 }  // namespace mdls
