@@ -145,6 +145,27 @@ def workload_flops(precs, n):
     return {p: opcount.lstsq_table1_flops(p, n, n) for p in precs}
 
 
+# md mul-add pairs of the paper's blocked QR at m = n, tile 128, back-solved
+# from its own timings and TFLOPS figures (context only: the algorithmic
+# count of the unblocked method, used for `value`, is about (4/3) n^3 mul-add
+# pairs, 14-17x fewer).
+PAPER_QR_PAIRS = {512: 2.55e9, 1024: 2.395e10, 1536: 7.48e10, 2048: 1.70e11}
+
+
+def paper_equivalent(precs, n, per_prec_ms, steps):
+    """TFLOPS in the paper's own counting (QR mul-add pairs x Table-1 add+mul
+    flops / time of the least-squares solve), for comparison with its tables
+    only."""
+    if n not in PAPER_QR_PAIRS:
+        return None
+    from paper_2110_08375_gb300 import opcount
+    out = {"note": "paper-equivalent op count (back-solved from the paper's timings), context only"}
+    for p in precs:
+        sig = opcount.TABLE1_SIGMA[p]
+        out[PREC_NAMES[p]] = PAPER_QR_PAIRS[n] * (sig["add"] + sig["mul"]) / (per_prec_ms[p] / steps / 1e3) / 1e12
+    return out
+
+
 def cpu_baseline(n_sample: int, precs, seed: int = 0) -> dict:
     """The oracle (plain C, OpenMP) on a bounded sample of the workload: the
     leading n_sample x n_sample block of each precision's A and the leading
@@ -294,6 +315,7 @@ def run_gpu(args):
            "per_prec": {PREC_NAMES[p]: {"ms": per_prec_ms[p] / args.steps,
                                         "tflops": fl[p] / (per_prec_ms[p] / args.steps / 1e3) / 1e12}
                         for p in precs},
+           "paper_equivalent": paper_equivalent(precs, n, per_prec_ms, args.steps),
            "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()}}
 
     # end to end through the public API with host buffers: H2D of A and b, the
@@ -434,16 +456,38 @@ def run_batched(args, dev, stream, flush):
     e1.record(stream)
     torch.cuda.synchronize()
     loop_ms = e0.elapsed_time(e1)
+    # the same loop in split mode (the mode the tuner may pick for the graph)
+    need_s = max(mdls.mdls_lstsq_workspace(p, m, n, 0, mdls.MODE_SPLIT) for (m, n, p) in shapes)
+    ws_s = mdls.workspace(need_s, dev)
+    xs_split = [torch.zeros_like(x) for (_, _, x) in probs]
+
+    def loop_split():
+        for (A, b_, _), xs in zip(probs, xs_split):
+            mdls.mdls_lstsq(A, b_, xs, tile=0, mode=mdls.MODE_SPLIT, ws=ws_s)
+    loop_split()
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0.record(stream)
+    loop_split()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_split_ms = e0.elapsed_time(e1)
+    del ws_s
     worst = 0.0
     for xb, (_, _, x) in zip(batched_x, probs):
         d = (xb - x).sum(dim=0).abs().max().item() / max(x[0].abs().max().item(), 1e-300)
         worst = max(worst, d)
     tiles = plan.tiles()
+    modes = plan.modes()
     res = {"problems": len(shapes), "solves_per_s": len(shapes) / (graph_ms / 1e3),
            "loop_solves_per_s": len(shapes) / (loop_ms / 1e3), "speedup_vs_loop": loop_ms / graph_ms,
+           "loop_split_solves_per_s": len(shapes) / (loop_split_ms / 1e3),
+           "speedup_vs_split_loop": loop_split_ms / graph_ms,
            "graph_ms": graph_ms, "loop_ms": loop_ms, "plan_s_with_autotune": plan_s,
            "max_rel_diff_batched_vs_loop": worst, "nonzero_status": sum(1 for s in status if s != 0),
-           "tiles_used": sorted(set(tiles))}
+           "tiles_used": sorted(set(tiles)),
+           "modes_used": {"plain": sum(1 for m in modes if m == mdls.MODE_PLAIN),
+                          "split": sum(1 for m in modes if m == mdls.MODE_SPLIT)}}
     plan.destroy()
     return res
 
@@ -494,12 +538,18 @@ def run_backsub(args, dev, stream, flush, p=4, n=17920, t=128):
     k = len(ms)
     med = statistics.median(ms)
     flops = opcount.table1_flops(p, opcount.backsub_counts(n))
+    # the paper's count for Algorithm 1 also credits the tile inversions
+    # (t^3/2 mul-add pairs per tile): context only
+    sig = opcount.TABLE1_SIGMA[p]
+    ntiles = -(-n // t)
+    paper_pairs = ntiles * t ** 3 / 2 + n * (n - 1) / 2
     rbytes = n * (n + 1) // 2 * 8 * p
     del R
     torch.cuda.empty_cache()
     return {"workload": f"qd back substitution n={n}, tile {t} ({-(-n // t)} tiles), R resident in HBM, "
                         "L2 flushed before each solve",
             "ms": med, "table1_tflops": flops / (med / 1e3) / 1e12,
+            "paper_equivalent_tflops": paper_pairs * (sig["add"] + sig["mul"]) / (med / 1e3) / 1e12,
             "hbm_gbs_upper_triangle": rbytes / (med / 1e3) / 1e9, "status": status,
             "stages_ms": {kk: round(v[0] / k, 3) for kk, v in stages.items() if v[0] > 0}}
 

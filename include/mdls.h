@@ -195,12 +195,14 @@ int mdls_vec_op(int prec, int op, int64_t count, const double* a, int64_t psa, c
  *   written); tile 0 lets the autotuner choose.
  *   mdls_batched_workspace(): bytes of caller workspace for the problems
  *   (0 if one of them is invalid).
- *   mdls_batched_plan(): checks the problems, picks each tile -- the caller's,
- *   else the autotuner's choice for the size class (prec, n rounded down to
- *   a power of two): when autotune != 0, the first problem of a class never
- *   seen before in this process is solved with each candidate tile (8, 16,
- *   32) on its own buffers and timed, and the fastest tile serves the whole
- *   class; otherwise a fixed rule -- then captures every problem's kernels into one CUDA graph
+ *   mdls_batched_plan(): checks the problems, picks each tile and mode --
+ *   when autotune != 0, the autotuner's choice for the size class (prec, n
+ *   rounded down to a power of two, the caller's tile if fixed): the first
+ *   problem of a class never seen before in this process is solved with each
+ *   candidate tile (8, 16, 32; or the caller's) in each mode (plain, split:
+ *   the same accuracy) on its own buffers and timed, and the fastest pair
+ *   serves the whole class; otherwise the caller's tile or a fixed rule, in
+ *   plain mode -- then captures every problem's kernels into one CUDA graph
  *   (parallel branches, largest problems first, each problem with its own
  *   slice of ws and a single-block panel) and instantiates it.  Planning
  *   synchronises the device and must not run inside a stream capture.
@@ -208,6 +210,8 @@ int mdls_vec_op(int prec, int op, int64_t count, const double* a, int64_t psa, c
  *   mdls_batched_status(): waits for stream, then copies each problem's
  *   device status (MDLS_OK, MDLS_ERR_SINGULAR, ...) to status[count] (host).
  *   mdls_batched_tiles(): the tile of each problem, to tiles[count] (host).
+ *   mdls_batched_modes(): the mode of each problem (MDLS_MODE_PLAIN or
+ *   MDLS_MODE_SPLIT), to modes[count] (host).
  *   mdls_batched_destroy(): frees the plan (not the caller's buffers).
  * The plan keeps pointers to the problems' buffers and to ws: they must stay
  * valid and must not move while the plan is used.
@@ -230,6 +234,7 @@ int mdls_batched_plan(const mdls_problem* probs, int count, void* ws, size_t ws_
 int mdls_batched_launch(void* plan, void* stream);
 int mdls_batched_status(void* plan, int* status, void* stream);
 int mdls_batched_tiles(void* plan, int* tiles);
+int mdls_batched_modes(void* plan, int* modes);
 void mdls_batched_destroy(void* plan);
 
 /*

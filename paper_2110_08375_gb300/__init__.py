@@ -83,6 +83,7 @@ def lib() -> C.CDLL:
     L.mdls_batched_launch.argtypes = [vp, vp]
     L.mdls_batched_status.argtypes = [vp, C.POINTER(C.c_int), vp]
     L.mdls_batched_tiles.argtypes = [vp, C.POINTER(C.c_int)]
+    L.mdls_batched_modes.argtypes = [vp, C.POINTER(C.c_int)]
     L.mdls_batched_destroy.argtypes = [vp]
     L.mdls_batched_destroy.restype = None
     L.mdls_vec_op.argtypes = [C.c_int, C.c_int, i64, vp, i64, vp, i64, vp, i64, vp]
@@ -294,6 +295,11 @@ class BatchedPlan:
     def tiles(self):
         out = (C.c_int * self.count)()
         lib().mdls_batched_tiles(self.handle, out)
+        return list(out)
+
+    def modes(self):
+        out = (C.c_int * self.count)()
+        lib().mdls_batched_modes(self.handle, out)
         return list(out)
 
     def destroy(self):

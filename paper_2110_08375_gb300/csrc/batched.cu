@@ -11,9 +11,12 @@
 //
 // Autotuner: for every (precision, n-bucket) class not seen before (n
 // buckets are powers of two), the first problem of that class is solved with
-// each candidate tile (8, 16, 32 that fit) on the problem's own buffers,
-// timed with CUDA events after one warm-up, and the fastest tile is kept in
-// a process-wide table for every later problem of the class.
+// each candidate (tile 8, 16, 32 that fit) x (mode plain, split) on the
+// problem's own buffers, timed with CUDA events after one warm-up, and the
+// fastest pair is kept in a process-wide table for every later problem of
+// the class.  Both modes meet the same accuracy; split runs the WY products
+// on the tensor cores and pays for digit conversions, which small problems
+// may not repay.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,13 +43,14 @@ using namespace mdls;
 namespace {
 
 const int kCandidates[] = {8, 16, 32};
+const int kModes[] = {MDLS_MODE_PLAIN, MDLS_MODE_SPLIT};
 constexpr int kBranches = 32;
 
-int solve_one(const mdls_problem& p, int tile, void* ws, cudaStream_t st) {
+int solve_one(const mdls_problem& p, int tile, int mode, void* ws, cudaStream_t st) {
     switch (p.prec) {
-        case 2: return ls_entry_p2(p.m, p.n, p.A, p.lda, p.psa, p.b, p.psb, p.x, p.psx, tile, 0, ws, st, true);
-        case 4: return ls_entry_p4(p.m, p.n, p.A, p.lda, p.psa, p.b, p.psb, p.x, p.psx, tile, 0, ws, st, true);
-        default: return ls_entry_p8(p.m, p.n, p.A, p.lda, p.psa, p.b, p.psb, p.x, p.psx, tile, 0, ws, st, true);
+        case 2: return ls_entry_p2(p.m, p.n, p.A, p.lda, p.psa, p.b, p.psb, p.x, p.psx, tile, mode, ws, st, true);
+        case 4: return ls_entry_p4(p.m, p.n, p.A, p.lda, p.psa, p.b, p.psb, p.x, p.psx, tile, mode, ws, st, true);
+        default: return ls_entry_p8(p.m, p.n, p.A, p.lda, p.psa, p.b, p.psb, p.x, p.psx, tile, mode, ws, st, true);
     }
 }
 
@@ -56,12 +60,18 @@ bool problem_ok(const mdls_problem& p) {
            p.tile <= 256;
 }
 
+// Workspace of one problem: the largest over the candidates it may run.
 size_t problem_ws(const mdls_problem& p) {
     size_t best = 0;
-    if (p.tile > 0) return align256(ls_layout(p.prec, p.m, p.n, norm_tile(p.tile, p.n)).total);
-    for (int c : kCandidates) {
-        const int t = norm_tile(c, p.n);
-        best = std::max(best, ls_layout(p.prec, p.m, p.n, t).total);
+    for (int mode : kModes) {
+        if (p.tile > 0) {
+            best = std::max(best, ls_layout(p.prec, p.m, p.n, norm_tile(p.tile, p.n), mode == MDLS_MODE_SPLIT).total);
+            continue;
+        }
+        for (int c : kCandidates) {
+            const int t = norm_tile(c, p.n);
+            best = std::max(best, ls_layout(p.prec, p.m, p.n, t, mode == MDLS_MODE_SPLIT).total);
+        }
     }
     return align256(best);
 }
@@ -73,51 +83,56 @@ int bucket(int64_t v) {  // powers of two
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int>, int> g_tune;  // (prec, n bucket) -> tile
+struct Choice {
+    int tile, mode;
+};
+std::map<std::tuple<int, int, int>, Choice> g_tune;  // (prec, n bucket, fixed tile) -> choice
 
 int heuristic_tile(const mdls_problem& p) {
     const int t = p.n <= 64 ? 16 : (p.n <= 256 ? 32 : 64);
     return norm_tile(t, p.n);
 }
 
-int autotune(const mdls_problem& p, void* ws, int* rc) {
+Choice autotune(const mdls_problem& p, void* ws, int* rc) {
     cudaStream_t st;
     *rc = MDLS_OK;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
         *rc = MDLS_ERR_CUDA;
-        return heuristic_tile(p);
+        return Choice{p.tile > 0 ? norm_tile(p.tile, p.n) : heuristic_tile(p), MDLS_MODE_PLAIN};
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best_t = heuristic_tile(p);
+    Choice best{p.tile > 0 ? norm_tile(p.tile, p.n) : heuristic_tile(p), MDLS_MODE_PLAIN};
     float best_ms = 1e30f;
-    int last = -1;
-    for (int c : kCandidates) {
-        const int t = norm_tile(c, p.n);
-        if (t == last) continue;
-        last = t;
-        if (solve_one(p, t, ws, st) != MDLS_OK) continue;
-        float ms = 0.f;
-        cudaEventRecord(e0, st);
-        bool ok = solve_one(p, t, ws, st) == MDLS_OK;
-        cudaEventRecord(e1, st);
-        ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-        if (!ok) continue;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best_t = t;
+    for (int mode : kModes) {
+        int last = -1;
+        for (int c : kCandidates) {
+            const int t = p.tile > 0 ? norm_tile(p.tile, p.n) : norm_tile(c, p.n);
+            if (t == last) continue;
+            last = t;
+            if (solve_one(p, t, mode, ws, st) != MDLS_OK) continue;
+            float ms = 0.f;
+            cudaEventRecord(e0, st);
+            bool ok = solve_one(p, t, mode, ws, st) == MDLS_OK;
+            cudaEventRecord(e1, st);
+            ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            if (!ok) continue;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = Choice{t, mode};
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(st);
-    return best_t;
+    return best;
 }
 
 struct Plan {
     std::vector<mdls_problem> probs;
-    std::vector<int> tiles;
+    std::vector<int> tiles, modes;
     std::vector<size_t> ws_off;
     char* ws = nullptr;
     cudaGraph_t graph = nullptr;
@@ -157,27 +172,24 @@ int mdls_batched_plan(const mdls_problem* probs, int count, void* ws, size_t ws_
         off += problem_ws(probs[i]);
     }
     const bool was_timing = profiler_pause();
-    // tiles
+    // tile and mode of every problem
     int rc = MDLS_OK;
     for (int i = 0; i < count && rc == MDLS_OK; ++i) {
         const mdls_problem& p = P->probs[i];
-        int t;
-        if (p.tile > 0) {
-            t = norm_tile(p.tile, p.n);
-        } else {
-            const auto key = std::make_tuple(p.prec, bucket(p.n));
+        Choice ch{p.tile > 0 ? norm_tile(p.tile, p.n) : heuristic_tile(p), MDLS_MODE_PLAIN};
+        if (autotune_tiles) {
+            const auto key = std::make_tuple(p.prec, bucket(p.n), p.tile);
             std::lock_guard<std::mutex> g(g_tune_mu);
             auto it = g_tune.find(key);
             if (it != g_tune.end()) {
-                t = norm_tile(it->second, p.n);
-            } else if (autotune_tiles) {
-                t = autotune(p, P->ws + P->ws_off[i], &rc);
-                g_tune[key] = t;
+                ch = Choice{p.tile > 0 ? norm_tile(p.tile, p.n) : norm_tile(it->second.tile, p.n), it->second.mode};
             } else {
-                t = heuristic_tile(p);
+                ch = autotune(p, P->ws + P->ws_off[i], &rc);
+                g_tune[key] = ch;
             }
         }
-        P->tiles.push_back(t);
+        P->tiles.push_back(ch.tile);
+        P->modes.push_back(ch.mode);
     }
     // capture: problems, largest first, onto the least loaded branch
     std::vector<int> order(count);
@@ -214,7 +226,7 @@ int mdls_batched_plan(const mdls_problem* probs, int count, void* ws, size_t ws_
             used[b] = true;
         }
         load[b] += cost(i);
-        rc = solve_one(P->probs[i], P->tiles[i], P->ws + P->ws_off[i], br[b]);
+        rc = solve_one(P->probs[i], P->tiles[i], P->modes[i], P->ws + P->ws_off[i], br[b]);
     }
     for (int b = 0; b < kBranches && rc == MDLS_OK; ++b) {
         if (!used[b]) continue;
@@ -268,6 +280,13 @@ int mdls_batched_tiles(void* plan, int* tiles) {
     Plan* P = static_cast<Plan*>(plan);
     if (!P || !tiles) return MDLS_ERR_ARG;
     for (size_t i = 0; i < P->tiles.size(); ++i) tiles[i] = P->tiles[i];
+    return MDLS_OK;
+}
+
+int mdls_batched_modes(void* plan, int* modes) {
+    Plan* P = static_cast<Plan*>(plan);
+    if (!P || !modes) return MDLS_ERR_ARG;
+    for (size_t i = 0; i < P->modes.size(); ++i) modes[i] = P->modes[i];
     return MDLS_OK;
 }
 

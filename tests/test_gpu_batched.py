@@ -1,6 +1,7 @@
 """Batched least squares: mixed shapes and precisions in one graph launch,
-each solution checked against the oracle; explicit and autotuned tiles; a
-replay gives identical bits; invalid problems are rejected at planning."""
+each solution checked against the oracle; explicit and autotuned tiles and
+modes; a replay gives identical bits; invalid problems are rejected at
+planning."""
 import numpy as np
 import pytest
 
@@ -33,6 +34,7 @@ def test_batched_matches_oracle():
         assert oracle.rel_err(to_host(x), oracle.lstsq(A, b)) < TOL[p], (m, n, p)
     tiles = plan.tiles()
     assert all(1 <= t <= n for t, (m, n, p) in zip(tiles, shapes))
+    assert set(plan.modes()) <= {mdls.MODE_PLAIN, mdls.MODE_SPLIT}
     # a replay is bitwise identical
     first = [to_host(x).copy() for (_, _, x) in probs]
     for (_, _, x) in probs:
