@@ -19,12 +19,14 @@
 // split_gemm_kernel computes one 16 x 8 output tile per block with
 // mma.sync m16n8k16 (bf16 in, fp32 accumulate), the 8 warps sharing the
 // diagonals q round-robin; each warp moves its fp32 sums into int64 after
-// every k16 step (at most 16 S products, exact), and the epilogue turns the
-// S diagonal sums into P limbs with the exact md renormalisation.
+// every k16 step (at most 16 S products, exact), and the epilogue places the
+// S exact diagonal sums into 24-bit digits on the integer pipe and truncates
+// the exact total to P limbs.
 #pragma once
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "fx.cuh"
 
 namespace mdls {
 
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(256)
                 // at most 16 S <= 880 products of |.| <= 2^14 since the last move: exact
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    acci[jj][c] += (long long)accf[jj][c];
+                    acci[jj][c] += (long long)__float2int_rz(accf[jj][c]);  // an integer below 2^24: exact in int32
                     accf[jj][c] = 0.f;
                 }
             }
@@ -224,13 +226,32 @@ __global__ void __launch_bounds__(256)
         const int r = tid / kSplitTn, cc = tid % kSplitTn;
         const int64_t i = i0 + r, j = j0 + cc;
         if (i < M && j < N) {
-            double terms[S];
-#pragma unroll
-            for (int q = 0; q < S; ++q) terms[q] = ldexp((double)Dsm[(size_t)q * (kSplitTm * kSplitTn) + tid], -8 * (q + 2));
-            md<P> v = renorm_n<S, P>(terms);
+            // the value 2^sc sum_q D_q 2^(-8(q+2)) exactly, as 24-bit digits on
+            // the integer pipe (D_q is an integer below 2^40 in magnitude),
+            // then truncated to P limbs: no FP64 work for the S sums.  D_q
+            // sits at bit 8(S-1-q) of sum_q D_q 2^(8(S-1-q)) (compile-time
+            // digit positions); the whole sum is then shifted by the 0..23
+            // bits that put its weight 2^(sc - 8(S+1)) on a digit boundary.
+            constexpr int N = fx::Cfg<P>::N;
+            constexpr int ND = (8 * (S - 1) + 23) / 24 + 4;
             const int sc = ea[i] + fb[j];
+            const int bmin = sc - 8 * (S + 1);  // weight of D_(S-1)
+            const int E = fx::floordiv24(bmin);
+            const int boff = bmin - 24 * E;      // 0..23
+            int64_t c[ND];
 #pragma unroll
-            for (int l = 0; l < P; ++l) v.v[l] = ldexp(v.v[l], sc);
+            for (int k = 0; k < ND; ++k) c[k] = 0;
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                const int sh = 8 * (S - 1 - q), k = sh / 24, rem = sh % 24;
+                const int64_t dq = Dsm[(size_t)q * (kSplitTm * kSplitTn) + tid];
+                c[k] += (dq & (((int64_t)1 << (24 - rem)) - 1)) << rem;
+                c[k + 1] += dq >> (24 - rem);
+            }
+            fx::carry_norm<ND>(c);
+#pragma unroll
+            for (int k = 0; k < ND; ++k) c[k] *= (int64_t)1 << boff;
+            md<P> v = fx::xf_to_md<P, N>(fx::xf_from_acc<N, ND>(c, E));
             if (negate) v = md_neg<P>(v);
             const int64_t off = j * C.ld + i;
             if (accumulate) v = md_add<P>(ld_md<P>(C.ptr, C.ps, off), v);
