@@ -346,7 +346,7 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
 
 // Tiled back substitution (Algorithm 1) of R x = y, R upper triangular n x n.
 // Step 1: invert the N diagonal tiles into D (tile i at D + i t^2, ld t):
-// leaves of 16 columns, then the recursive levels, all tiles at once.
+// leaves of kTriLeaf columns, then the recursive levels, all tiles at once.
 template <int P>
 int bs_invert(int64_t n, const double* R, int64_t ldr, int64_t psr, int t, char* ws,
               const BsLayout& L, WsHeader* hdr, cudaStream_t st) {

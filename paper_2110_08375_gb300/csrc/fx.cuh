@@ -512,6 +512,58 @@ FX_CALL md<P> xf_to_md(const xf<N>& x) {
     return r;
 }
 
+// The same Householder scalars computed in P-limb arithmetic on the FP64
+// pipe (csrc/md.cuh) from the digit inputs rounded to P limbs, and returned
+// exactly as digits.  The results carry P-limb accuracy (about 2^(2-53P)
+// relative) instead of 24(N-1) bits, and the reflector they define is
+// orthogonal to the accuracy of the P-limb output.  For double double they
+// take a few hundred FP64 instructions on one thread, far fewer cycles than
+// the digit Newton iterations (the panels use them for P = 2 only).  Same
+// kinds and formulas as xf_house (one reciprocal in either branch).
+template <int P, int N>
+FX_CALL int xf_house_md(const xf<N>& sig_x, const xf<N>& x0_x, xf<N>& v0, xf<N>& bp, xf<N>& rcc,
+                        xf<N>& inv_v0, xf<N>& beta) {
+    if (xf_is_zero(sig_x)) {
+        v0 = xf_from_int<N>(1);
+        inv_v0 = v0;
+        if (xf_sign(x0_x) >= 0) {
+            bp = xf_zero<N>();
+            rcc = x0_x;
+            beta = bp;
+            return 1;
+        }
+        bp = xf_from_int<N>(2);
+        rcc = xf_neg<N>(x0_x);
+        beta = bp;
+        return 2;
+    }
+    const md<P> sig = xf_to_md<P, N>(sig_x), x0 = xf_to_md<P, N>(x0_x);
+    const md<P> one = md_from_double<P>(1.0);
+    const md<P> a2 = md_fma<P>(sig, x0, x0);
+    const md<P> mu = md_sqrt<P>(a2);
+    md<P> v0m, bpm, invm;
+    if (xf_sign(x0_x) <= 0) {
+        v0m = md_sub<P>(x0, mu);
+        const md<P> R = md_div<P>(one, md_mul<P>(mu, v0m));
+        bpm = md_neg<P>(R);
+        invm = md_mul<P>(mu, R);
+    } else {
+        const md<P> sx = md_add<P>(x0, mu);
+        const md<P> R = md_div<P>(one, md_mul<P>(sig, sx));
+        v0m = md_neg<P>(md_mul<P>(sig, md_mul<P>(sig, R)));
+        const md<P> s2R = md_mul<P>(sx, md_mul<P>(sx, R));
+        invm = md_neg<P>(s2R);
+        bpm = md_div<P>(s2R, mu);
+    }
+    const md<P> betam = md_mul<P>(md_mul<P>(bpm, v0m), v0m);
+    v0 = xf_from_md<P, N>(v0m);
+    bp = xf_from_md<P, N>(bpm);
+    inv_v0 = xf_from_md<P, N>(invm);
+    beta = xf_from_md<P, N>(betam);
+    rcc = xf_from_md<P, N>(mu);
+    return 0;
+}
+
 // ---------------------------------------------------------------------------
 // Panel entries (fixed point with a per-column digit scale e)
 // ---------------------------------------------------------------------------

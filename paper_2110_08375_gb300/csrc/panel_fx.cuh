@@ -84,6 +84,29 @@ DEV_INLINE void block_digit_sum(int64_t (&acc)[M], int64_t (*red)[M]) {
     __syncthreads();
 }
 
+// The reflector's scalars for one warp: in double-double FP64 arithmetic
+// for P = 2 (fx::xf_house_md: a few hundred FP64 instructions, every lane
+// computing the same values; 5x fewer cycles than the digit Newton steps),
+// in digits spread over the warp for quad and octo double, whose P-limb
+// divisions and square roots cost more than the digit Newton steps.
+template <int P, int N>
+DEV_INLINE int panel_house(const fxw::wxf& sig, const fxw::wxf& x0, fxw::wxf& v0, fxw::wxf& bp, fxw::wxf& rcc,
+                           fxw::wxf& inv, fxw::wxf& bet) {
+    if constexpr (P == 2) {
+        const fx::xf<N> s = fxw::to_scalar<N>(sig), x = fxw::to_scalar<N>(x0);
+        fx::xf<N> a, b, c, d, e;
+        const int kind = fx::xf_house_md<P, N>(s, x, a, b, c, d, e);
+        v0 = fxw::from_scalar<N>(a);
+        bp = fxw::from_scalar<N>(b);
+        rcc = fxw::from_scalar<N>(c);
+        inv = fxw::from_scalar<N>(d);
+        bet = fxw::from_scalar<N>(e);
+        return kind;
+    } else {
+        return fxw::house<N>(sig, x0, v0, bp, rcc, inv, bet);
+    }
+}
+
 template <int P, int NT>
 __global__ void __launch_bounds__(NT, 2) fx_panel_kernel(FxPanelArgs a) {
     using namespace fx;
@@ -273,7 +296,7 @@ __global__ void __launch_bounds__(NT, 2) fx_panel_kernel(FxPanelArgs a) {
         const fxw::wxf sig = fxw::from_acc<N, M>(tot, 2 * ec + D - 3);
         const int32_t xe = lane < D ? Fc[lane * fs + c] : 0;
         fxw::wxf v0, bp, rcc, inv, bet;
-        const int kind = fxw::house<N>(sig, fxw::from_fixed<N, D>(xe, ec), v0, bp, rcc, inv, bet);
+        const int kind = panel_house<P, N>(sig, fxw::from_fixed<N, D>(xe, ec), v0, bp, rcc, inv, bet);
         if (lane == 0) Mc[FxMeta<P>::kKind] = kind;
         wst_xf<N>(Mc + FxMeta<P>::kV0, v0);
         wst_xf<N>(Mc + FxMeta<P>::kBp, bp);
@@ -462,7 +485,7 @@ __global__ void __launch_bounds__(NT) fx_panel_block_kernel(FxBlockPanelArgs a) 
             const fxw::wxf sig = fxw::from_acc<N, M>(tot, 2 * ec + D - 3);
             const int32_t xe = lane < D ? Fc[lane * fs + c] : 0;
             fxw::wxf v0, bp, rcc, inv, bet;
-            const int kind = fxw::house<N>(sig, fxw::from_fixed<N, D>(xe, ec), v0, bp, rcc, inv, bet);
+            const int kind = panel_house<P, N>(sig, fxw::from_fixed<N, D>(xe, ec), v0, bp, rcc, inv, bet);
             if (lane < N) {
                 sh_v0[lane] = v0.d;
                 sh_bp[lane] = bp.d;

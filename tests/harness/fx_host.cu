@@ -129,14 +129,15 @@ extern "C" int fx_axpy(int p, long n, double* a, const double* u, const double* 
 
 // Householder scalars from sigma and x0 (entries i): v0, bp, R, 1/v0, beta
 // and the kind.
+// md_variant: the P-limb FP64 form (xf_house_md) instead of the digit form.
 template <int P>
 static void house(long n, const double* sig, const double* x0, double* v0, double* bp, double* rcc,
-                  double* inv, double* beta, int* kind) {
+                  double* inv, double* beta, int* kind, bool md_variant) {
     constexpr int N = Cfg<P>::N;
     for (long i = 0; i < n; ++i) {
         xf<N> V, B, R, I, Be;
-        kind[i] = xf_house<N>(xf_from_md<P, N>(load<P>(sig, n, i)), xf_from_md<P, N>(load<P>(x0, n, i)),
-                              V, B, R, I, Be);
+        const xf<N> S = xf_from_md<P, N>(load<P>(sig, n, i)), X = xf_from_md<P, N>(load<P>(x0, n, i));
+        kind[i] = md_variant ? xf_house_md<P, N>(S, X, V, B, R, I, Be) : xf_house<N>(S, X, V, B, R, I, Be);
         store<P>(v0, n, i, xf_to_md<P, N>(V));
         store<P>(bp, n, i, xf_to_md<P, N>(B));
         store<P>(rcc, n, i, xf_to_md<P, N>(R));
@@ -147,9 +148,16 @@ static void house(long n, const double* sig, const double* x0, double* v0, doubl
 
 extern "C" void fx_house(int p, long n, const double* sig, const double* x0, double* v0, double* bp,
                          double* rcc, double* inv, double* beta, int* kind) {
-    if (p == 2) house<2>(n, sig, x0, v0, bp, rcc, inv, beta, kind);
-    else if (p == 4) house<4>(n, sig, x0, v0, bp, rcc, inv, beta, kind);
-    else house<8>(n, sig, x0, v0, bp, rcc, inv, beta, kind);
+    if (p == 2) house<2>(n, sig, x0, v0, bp, rcc, inv, beta, kind, false);
+    else if (p == 4) house<4>(n, sig, x0, v0, bp, rcc, inv, beta, kind, false);
+    else house<8>(n, sig, x0, v0, bp, rcc, inv, beta, kind, false);
+}
+
+extern "C" void fx_house_md(int p, long n, const double* sig, const double* x0, double* v0, double* bp,
+                            double* rcc, double* inv, double* beta, int* kind) {
+    if (p == 2) house<2>(n, sig, x0, v0, bp, rcc, inv, beta, kind, true);
+    else if (p == 4) house<4>(n, sig, x0, v0, bp, rcc, inv, beta, kind, true);
+    else house<8>(n, sig, x0, v0, bp, rcc, inv, beta, kind, true);
 }
 
 // Sequential replay of the integer-digit panel (one panel of all n columns
@@ -236,8 +244,10 @@ static int panel_replay(long m, long n, double* A, double* beta) {
         int32_t xe[D];
         for (int k = 0; k < D; ++k) xe[k] = dig(c, c, k);
         xf<N> v0, bp, rcc, inv, bet;
-        kinds[c] = xf_house<N>(xf_from_acc<N>(sacc, 2 * ec + D - 3), xf_from_fixed<N, D>(xe, ec), v0, bp, rcc,
-                               inv, bet);
+        // as on the GPU: double-double FP64 scalars for P = 2, digits otherwise
+        const xf<N> sig_x = xf_from_acc<N>(sacc, 2 * ec + D - 3), x0_x = xf_from_fixed<N, D>(xe, ec);
+        kinds[c] = P == 2 ? xf_house_md<P, N>(sig_x, x0_x, v0, bp, rcc, inv, bet)
+                          : xf_house<N>(sig_x, x0_x, v0, bp, rcc, inv, bet);
         v0s[c] = v0;
         bps[c] = bp;
         store<P>(beta, n, c, xf_to_md<P, N>(bet));
