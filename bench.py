@@ -396,6 +396,16 @@ def run_gpu(args):
                 del wsm
             modes[mname] = res
         out["modes"] = modes
+        # each mode over the whole step (the same workload and accuracy
+        # tolerances as `value`; refine covers qd and od only)
+        out["modes_total"] = {}
+        for mname, res in modes.items():
+            plist = [p for p in precs if PREC_NAMES[p] in res]
+            ms = sum(res[PREC_NAMES[p]]["ms"] for p in plist)
+            if ms > 0:
+                out["modes_total"][mname] = {
+                    "precisions": "+".join(PREC_NAMES[p] for p in plist), "ms_per_step": ms,
+                    "value": sum(fl[p] for p in plist) / (ms / 1e3) / 1e12, "unit": "TFLOPS"}
 
     # batched: the mixed workload (n ~ log-uniform [32, 512], m = n + U{0..n},
     # half dd, half qd) solved by one graph launch, against a loop of single
