@@ -44,7 +44,7 @@ namespace {
 
 const int kCandidates[] = {8, 16, 32};
 const int kModes[] = {MDLS_MODE_PLAIN, MDLS_MODE_SPLIT};
-constexpr int kBranches = 32;
+constexpr int kBranches = 128;  // the device runs at most 128 kernels at once
 
 int solve_one(const mdls_problem& p, int tile, int mode, void* ws, cudaStream_t st) {
     switch (p.prec) {
