@@ -536,7 +536,8 @@ int vec_entry(int op, int64_t count, const double* a, int64_t psa, const double*
 // Least squares in P limbs by double-double factorisation and iterative
 // refinement of the augmented system [I A; A^T 0][r; x] = [b; 0] (Bjorck's
 // refinement, which converges for inconsistent systems too).  The QR of A
-// rounded to dd (its two leading limbs) gives x0 and r0 = b - A x0; then,
+// rounded to dd (its two leading limbs; WY products as split products on the
+// tensor cores) gives x0 and r0 = b - A x0; then,
 // `iters` times, with the residuals formed in P limbs
 //   f = b - r - A x,  g = -A^T r,
 // and the corrections solved in dd with the factors A = Q [R; 0]:

@@ -113,8 +113,9 @@ inline BsLayout bs_layout(int P, int64_t n, int t, size_t* total = nullptr) {
 }
 
 // Least squares by double-double factorisation and refinement in P limbs:
-// the dd QR of A (every tile's W kept), dd back substitution, and the
-// vectors of the refinement loop.
+// the dd QR of A (every tile's W kept; its WY products on the tensor cores,
+// the digit slices included), dd back substitution, and the vectors of the
+// refinement loop.
 struct RefLayout {
     QrLayout qr;
     size_t A2, res, f, g, c, h, d, up, splitP;
@@ -126,7 +127,7 @@ struct RefLayout {
 inline RefLayout ref_layout(int P, int64_t m, int64_t n, int t) {
     Bump B;
     RefLayout L;
-    L.qr = qr_layout_at(B, 2, m, n, t, false, 0, true);
+    L.qr = qr_layout_at(B, 2, m, n, t, false, 0, true, true);  // dd factorisation with split products
     const size_t d2 = 2 * sizeof(double), dP = (size_t)P * sizeof(double);
     L.A2 = B.take(d2 * (size_t)m * (size_t)n);
     L.res = B.take(dP * (size_t)m);
