@@ -91,6 +91,39 @@ int launch_split_gemm(int stage, cudaStream_t st, const TcBuf& tc, int64_t M, in
     return MDLS_OK;
 }
 
+// Digit slices of an operand used in several split products (converted once).
+struct TcOperand {
+    __nv_bfloat16* s;  // [S][rows][Kp]
+    int* e;            // per-row scales
+    int64_t rows, K, Kp;
+};
+
+template <int P, class AV>
+int split_convert(int stage, cudaStream_t st, const TcOperand& op, AV a) {
+    StageScope sc(stage, st);
+    split_rows_kernel<P, AV><<<(unsigned)((op.rows * 32 + 255) / 256), 256, 0, st>>>(op.rows, op.K, op.Kp, a,
+                                                                                     op.s, op.e);
+    MDLS_LAUNCH_CHECK();
+    return MDLS_OK;
+}
+
+// C = [C] +/- A B with A's slices already in `A` and B (K x N) converted here
+// into `bs` / `fb` (room for N columns).
+template <int P, class BV>
+int split_gemm_pre(int stage, cudaStream_t st, const TcOperand& A, __nv_bfloat16* bs, int* fb, int64_t N, BV b,
+                   Dense c, bool neg, bool acc) {
+    split_gemm_setup<P>();
+    StageScope sc(stage, st);
+    split_rows_kernel<P, ViewTranspose<BV>><<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(
+        N, A.K, A.Kp, ViewTranspose<BV>{b}, bs, fb);
+    MDLS_LAUNCH_CHECK();
+    dim3 grid((unsigned)((A.rows + kSplitTm - 1) / kSplitTm), (unsigned)((N + kSplitTn - 1) / kSplitTn));
+    split_gemm_kernel<P><<<grid, 256, split_gemm_smem<P>(), st>>>(A.rows, N, A.Kp, A.s, bs, A.e, fb, c,
+                                                                 neg ? 1 : 0, acc ? 1 : 0);
+    MDLS_LAUNCH_CHECK();
+    return MDLS_OK;
+}
+
 // One md matrix-vector product (N = 1).  Rows contiguous in memory: 32 rows
 // per block on the lanes, k split over the block's warps and, when the rows
 // alone would leave SM sub-partitions idle, over grid.y (partials in `sb`,
@@ -563,7 +596,6 @@ int ls_refine_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t 
     double* X = reinterpret_cast<double*>(w + L.qr.X);
     const double* Wb = reinterpret_cast<const double*>(w + L.qr.W);
     const int64_t psw = L.qr.wcols * m, psX = (int64_t)t * L.qr.xcols;
-    const SplitBuf sbP{reinterpret_cast<double*>(w + L.splitP), L.splitP_cap};
     const SplitBuf sb2{reinterpret_cast<double*>(w + L.qr.split), L.qr.split_cap};
     const size_t vb = sizeof(double);
 #define MDLS_CPY(dst, src, cnt) \
@@ -599,19 +631,28 @@ int ls_refine_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t 
         if (l < 2) { MDLS_CPY(x + l * psx, dx + l * n, n); }
         else if (cudaMemsetAsync(x + l * psx, 0, n * vb, st) != cudaSuccess) return MDLS_ERR_CUDA;
     }
+    // A and A^T as digit slices, once: the residual products below run on the
+    // tensor cores (exact digit products, as in the split mode)
+    const TcOperand tA{reinterpret_cast<__nv_bfloat16*>(w + L.dA), reinterpret_cast<int*>(w + L.eA), m, n,
+                       round16(n)};
+    const TcOperand tAT{reinterpret_cast<__nv_bfloat16*>(w + L.dAT), reinterpret_cast<int*>(w + L.eAT), n, m,
+                        round16(m)};
+    __nv_bfloat16* dv = reinterpret_cast<__nv_bfloat16*>(w + L.dv);
+    int* ev = reinterpret_cast<int*>(w + L.ev);
+    if ((rc = split_convert<P>(ST_REFINE, st, tA, ViewDense{A, lda, psa}))) return rc;
+    if ((rc = split_convert<P>(ST_REFINE, st, tAT, ViewDenseT{A, lda, psa}))) return rc;
     // r0 = b - A x0 in P limbs
     for (int l = 0; l < P; ++l) { MDLS_CPY(res + l * m, b + l * psb, m); }
-    if ((rc = launch_gemm<P>(ST_REFINE, st, sbP, m, 1, n, ViewDense{A, lda, psa}, ViewDense{x, n, psx},
-                             Dense{res, m, m}, true, true)))
+    if ((rc = split_gemm_pre<P>(ST_REFINE, st, tA, dv, ev, 1, ViewDense{x, n, psx}, Dense{res, m, m}, true, true)))
         return rc;
     for (int it = 0; it < iters; ++it) {
         // f = b - r - A x,  g = -A^T r  (P limbs)
         if ((rc = vec(MDLS_OP_SUB, m, b, psb, res, m, f, m))) return rc;
-        if ((rc = launch_gemm<P>(ST_REFINE, st, sbP, m, 1, n, ViewDense{A, lda, psa}, ViewDense{x, n, psx},
-                                 Dense{f, m, m}, true, true)))
+        if ((rc = split_gemm_pre<P>(ST_REFINE, st, tA, dv, ev, 1, ViewDense{x, n, psx}, Dense{f, m, m}, true,
+                                    true)))
             return rc;
-        if ((rc = launch_gemm<P>(ST_REFINE, st, sbP, n, 1, m, ViewDenseT{A, lda, psa}, ViewDense{res, m, m},
-                                 Dense{g, n, n}, true, false)))
+        if ((rc = split_gemm_pre<P>(ST_REFINE, st, tAT, dv, ev, 1, ViewDense{res, m, m}, Dense{g, n, n}, true,
+                                    false)))
             return rc;
         // [f1; f2] = Q^T f (dd)
         for (int l = 0; l < 2; ++l) { MDLS_CPY(c + l * m, f + l * m, m); }

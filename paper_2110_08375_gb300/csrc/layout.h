@@ -118,9 +118,11 @@ inline BsLayout bs_layout(int P, int64_t n, int t, size_t* total = nullptr) {
 // refinement loop.
 struct RefLayout {
     QrLayout qr;
-    size_t A2, res, f, g, c, h, d, up, splitP;
-    int64_t splitP_cap;
+    size_t A2, res, f, g, c, h, d, up;
     BsLayout bs;
+    // digit slices of A and A^T in P limbs (the residual products b - A x
+    // and A^T r on the tensor cores), of the vector operand, and the scales
+    size_t dA, dAT, dv, eA, eAT, ev;
     size_t total;
 };
 
@@ -137,9 +139,14 @@ inline RefLayout ref_layout(int P, int64_t m, int64_t n, int t) {
     L.h = B.take(d2 * (size_t)n);
     L.d = B.take(d2 * (size_t)n);
     L.up = B.take(dP * (size_t)m);
-    L.splitP_cap = 16 * (m > n ? m : n);
-    L.splitP = B.take(dP * (size_t)L.splitP_cap);
     L.bs = bs_layout_at(B, 2, n, t);
+    const int64_t S = split_slices(P), mp = round16(m), np = round16(n);
+    L.dA = B.take(2 * (size_t)S * (size_t)m * (size_t)np);
+    L.dAT = B.take(2 * (size_t)S * (size_t)n * (size_t)mp);
+    L.dv = B.take(2 * (size_t)S * (size_t)(mp > np ? mp : np));
+    L.eA = B.take(4 * (size_t)m);
+    L.eAT = B.take(4 * (size_t)n);
+    L.ev = B.take(4);
     L.total = B.off;
     return L;
 }
