@@ -289,7 +289,7 @@ def run_gpu(args):
 
     # roofline of the dominant stage (trailing-update md GEMMs, FP64 ALU bound)
     trail_ms = stages["trailing"][0]
-    trail_ops = sum(opcount.trailing_md_fmas(n, n, t, extra_cols=1) * opcount.fma_cost(p)[0]
+    trail_ops = sum(opcount.trailing_md_fmas(n, n, t, extra_cols=1) * opcount.gemm_fma_cost(p)
                     for p in precs) * args.steps
     dominant = max(stages, key=lambda k: stages[k][0])
     achieved = trail_ops / (trail_ms / 1e3) / 1e12 if trail_ms > 0 else None
@@ -416,7 +416,7 @@ def run_gpu(args):
         out["backsub_qd_17920"] = run_backsub(args, dev, stream, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(384, precs)
+        out["cpu_baseline"] = cpu_baseline(448, precs)
         out["cpu_baseline"].pop("seconds", None)
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(kGemmTile* gemm_tn<P>())
     if constexpr (AV::kZeroKAboveI) kend = kend < i0 + kGemmTile ? kend : i0 + kGemmTile;
     if constexpr (BV::kZeroKBelowI) kend = kend < j0 + TN ? kend : j0 + TN;
     if constexpr (BV::kZeroKAboveI) kbeg = kbeg > j0 ? kbeg : j0;
-    md<P> acc = md_zero<P>();
+    double bins[P];  // unnormalised accumulator, renormalised once per staged tile
+#pragma unroll
+    for (int l = 0; l < P; ++l) bins[l] = 0.0;
     for (int64_t k0 = kbeg; k0 < kend; k0 += kGemmTile) {
 #pragma unroll
         for (int idx = threadIdx.x; idx < kGemmTile * kGemmTile; idx += NT) {
@@ -144,10 +146,14 @@ __global__ void __launch_bounds__(kGemmTile* gemm_tn<P>())
                 av.v[l] = As[l][kk][tx];
                 bv.v[l] = Bs[l][ty][kk];
             }
-            acc = md_fma<P>(acc, av, bv);
+            md_fma_bins<P>(bins, av, bv);
         }
+        md_bins_renorm<P>(bins);
         __syncthreads();
     }
+    md<P> acc;
+#pragma unroll
+    for (int l = 0; l < P; ++l) acc.v[l] = bins[l];
     if (i < M && j < N) {
         const int64_t off = j * C.ld + i;
         if (gridDim.z > 1) {
@@ -180,8 +186,11 @@ __global__ void __launch_bounds__(32 * NW)
     int64_t ke = (kb + kchunk) < K ? (kb + kchunk) : K;
     if constexpr (AV::kZeroKBelowI) kb = kb > i0 ? kb : i0;
     if constexpr (AV::kZeroKAboveI) ke = ke < i0 + 32 ? ke : i0 + 32;
-    md<P> acc = md_zero<P>();
+    double bins[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) bins[l] = 0.0;
     if (i < M) {
+        int cnt = 0;
         for (int64_t k = kb + warp; k < ke; k += NW) {
             md<P> a, x;
 #pragma unroll
@@ -189,9 +198,11 @@ __global__ void __launch_bounds__(32 * NW)
                 a.v[l] = A.get(i, k, l);
                 x.v[l] = B.get(k, 0, l);
             }
-            acc = md_fma<P>(acc, a, x);
+            md_fma_bins<P>(bins, a, x);
+            if ((++cnt & 15) == 0) md_bins_renorm<P>(bins);
         }
     }
+    md<P> acc = md_from_bins<P>(bins);
     red[warp][lane] = acc;
     __syncthreads();
 #pragma unroll
@@ -220,7 +231,10 @@ __global__ void gemv_warps_kernel(int64_t M, int64_t K, AV A, BV B, Dense C, int
     int64_t kend = (kbeg + kchunk) < K ? (kbeg + kchunk) : K;
     if constexpr (AV::kZeroKBelowI) kbeg = kbeg > i ? kbeg : i;
     if constexpr (AV::kZeroKAboveI) kend = kend < i + 1 ? kend : i + 1;
-    md<P> acc = md_zero<P>();
+    double bins[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) bins[l] = 0.0;
+    int cnt = 0;
     for (int64_t k = kbeg + lane; k < kend; k += 32) {
         md<P> a, x;
 #pragma unroll
@@ -228,9 +242,10 @@ __global__ void gemv_warps_kernel(int64_t M, int64_t K, AV A, BV B, Dense C, int
             a.v[l] = A.get(i, k, l);
             x.v[l] = B.get(k, 0, l);
         }
-        acc = md_fma<P>(acc, a, x);
+        md_fma_bins<P>(bins, a, x);
+        if ((++cnt & 15) == 0) md_bins_renorm<P>(bins);
     }
-    acc = warp_sum<P>(acc);
+    md<P> acc = warp_sum<P>(md_from_bins<P>(bins));
     if (lane != 0) return;
     if (gridDim.y > 1) {
         st_md<P>(C.ptr + blockIdx.y * zstride, C.ps, i, acc);
@@ -375,24 +390,26 @@ __global__ void __launch_bounds__(256) tri_level_kernel(double* X, int64_t ldx, 
     double* Xb = X + b * xtile;
     const double* Mb = M + b * mtile;
     const bool out = i < s && j < s2;
-    md<P> acc = md_zero<P>();
+    double bins[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) bins[l] = 0.0;
     if (out) {
-        const int kc = (s + KS - 1) / KS;
+        const int kc = (s + KS - 1) / KS;  // at most 16
         int kb = kz * kc, ke = kb + kc;
         if (STEP == 0) {
             ke = ke < j + 1 ? ke : j + 1;
             for (int k = kb; k < ke; ++k)
-                acc = md_fma<P>(acc, ld_md<P>(Mb, psm, (a + s + k) * ldm + a + i),
-                                ld_md<P>(Xb, psx, (a + s + j) * ldx + a + s + k));
+                md_fma_bins<P>(bins, ld_md<P>(Mb, psm, (a + s + k) * ldm + a + i),
+                               ld_md<P>(Xb, psx, (a + s + j) * ldx + a + s + k));
         } else {
             kb = kb > i ? kb : i;
             ke = ke < s ? ke : s;
             for (int k = kb; k < ke; ++k)
-                acc = md_fma<P>(acc, ld_md<P>(Xb, psx, (a + k) * ldx + a + i),
-                                ld_md<P>(Xb, psx, (a + k) * ldx + a + s + j));
+                md_fma_bins<P>(bins, ld_md<P>(Xb, psx, (a + k) * ldx + a + i),
+                               ld_md<P>(Xb, psx, (a + k) * ldx + a + s + j));
         }
     }
-    red[kz * 32 + lane] = acc;
+    red[kz * 32 + lane] = md_from_bins<P>(bins);
     __syncthreads();
     for (int hh = KS / 2; hh > 0; hh >>= 1) {
         if (kz < hh) red[kz * 32 + lane] = md_add<P>(red[kz * 32 + lane], red[(kz + hh) * 32 + lane]);

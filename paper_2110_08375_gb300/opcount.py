@@ -103,6 +103,14 @@ def fma_cost(p: int, with_c: bool = True):
     return _add(cost, renorm_cost(p))
 
 
+def gemm_fma_cost(p: int, renorm_every: int = 16):
+    """FP64 instructions per md FMA of the product loops (csrc/kernels.cuh:
+    md_fma_bins, one renormalisation per `renorm_every` steps)."""
+    full = fma_cost(p)[0]
+    rn = renorm_cost(p)[0]
+    return full - rn + rn / renorm_every
+
+
 def add_cost(p: int):
     cost = (0, 0)
     ne = 0

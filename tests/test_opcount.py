@@ -61,3 +61,12 @@ def test_device_fma_cost_structure():
     assert opcount.fma_cost(2) == (2 + 6 + 2 + 2 + 6, 3 + 6 + 4 + 2 + 6)
     assert opcount.add_cost(2) == (6 + 2 + 6, 6 + 2 + 6)
     assert opcount.fma_cost(4)[0] < opcount.fma_cost(8)[0]
+
+
+def test_gemm_loop_cost_defers_renormalisation():
+    """The product loops renormalise once per 16 steps: per md FMA they issue
+    the bins of md_fma plus a sixteenth of its renormalisation."""
+    for p in (2, 4, 8):
+        full, rn = opcount.fma_cost(p)[0], opcount.renorm_cost(p)[0]
+        assert opcount.gemm_fma_cost(p) == full - rn + rn / 16
+        assert opcount.gemm_fma_cost(p, renorm_every=1) == full
