@@ -547,6 +547,24 @@ def run_backsub(args, dev, stream, flush, p=4, n=17920, t=128):
     mdls.mdls_profile_enable(False)
     k = len(ms)
     med = statistics.median(ms)
+    # the paper's tile study (its back-substitution experiments vary the tile
+    # size at fixed n): the same solve with other tiles, same resident R
+    sweep = {t: med}
+    for t2 in (32, 64, 256):
+        ws2 = mdls.workspace(mdls.mdls_backsub_workspace(p, n, t2), dev)
+        x2 = torch.zeros_like(x)
+        mdls.mdls_backsub(R, y, x2, tile=t2, ws=ws2)
+        torch.cuda.synchronize()
+        ms2 = []
+        for _ in range(3):
+            flush.zero_()
+            e0.record(stream)
+            mdls.mdls_backsub(R, y, x2, tile=t2, ws=ws2)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms2.append(e0.elapsed_time(e1))
+        sweep[t2] = statistics.median(ms2)
+        del ws2
     flops = opcount.table1_flops(p, opcount.backsub_counts(n))
     # the paper's count for Algorithm 1 also credits the tile inversions
     # (t^3/2 mul-add pairs per tile): context only
@@ -561,6 +579,7 @@ def run_backsub(args, dev, stream, flush, p=4, n=17920, t=128):
             "ms": med, "table1_tflops": flops / (med / 1e3) / 1e12,
             "paper_equivalent_tflops": paper_pairs * (sig["add"] + sig["mul"]) / (med / 1e3) / 1e12,
             "hbm_gbs_upper_triangle": rbytes / (med / 1e3) / 1e9, "status": status,
+            "tile_sweep_ms": {str(k2): round(v2, 3) for k2, v2 in sorted(sweep.items())},
             "stages_ms": {kk: round(v[0] / k, 3) for kk, v in stages.items() if v[0] > 0}}
 
 

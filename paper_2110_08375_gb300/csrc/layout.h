@@ -161,6 +161,17 @@ inline LsLayout ls_layout(int P, int64_t m, int64_t n, int t, bool split = false
     return L;
 }
 
+// Back substitution alone: tile 0 = 64.  Measured on qd n = 17920: tiles
+// 32, 64, 128, 256 take 74, 67, 74, 103 ms -- narrower tiles halve the tile
+// inversions' work (n t^2 / 6 md FMAs) until the latency of the 2n/t
+// dependent tile steps takes over.
+inline int norm_tile_bs(int tile, int64_t n) {
+    if (tile < 0 || tile > 256) return -1;
+    int t = tile == 0 ? 64 : tile;
+    if (n > 0 && t > n) t = (int)n;
+    return t;
+}
+
 // tile 0 = default; a tile wider than the problem is clipped to it
 inline int norm_tile(int tile, int64_t n) {
     if (tile < 0 || tile > 256) return -1;
