@@ -565,6 +565,90 @@ FX_CALL int xf_house_md(const xf<N>& sig_x, const xf<N>& x0_x, xf<N>& v0, xf<N>&
 }
 
 // ---------------------------------------------------------------------------
+// Double-double Householder scalars with short dependency chains
+// ---------------------------------------------------------------------------
+// One thread (or one warp in lockstep) computes the scalars, so their cost is
+// the length of the chain of dependent FP64 operations, each waiting out the
+// pipe's latency (about 63 cycles measured here; an IEEE division or square
+// root about 630).  Hence: one Newton correction of the double reciprocal or
+// square root instead of long division, and v0, bp, 1/v0, beta from mu, 1/mu
+// and products instead of further divisions.
+
+// Dekker's fast two-sum: s + e == a + b exactly when |a| >= |b| (or a == 0).
+MD_INLINE md<2> dd_fast_sum(double a, double b) {
+    const double s = dadd(a, b);
+    return md<2>{{s, dsub(b, dsub(s, a))}};
+}
+
+// a * b: the exact product of the leading limbs plus the two cross terms
+// (a1 b1, below 2^-106 |ab|, is dropped); relative error below 2^-103.
+MD_INLINE md<2> dd_mul(const md<2>& a, const md<2>& b) {
+    double p, e;
+    two_prod(a.v[0], b.v[0], p, e);
+    e = dfma(a.v[0], b.v[1], dfma(a.v[1], b.v[0], e));
+    return dd_fast_sum(p, e);
+}
+
+// 1 / b (b nonzero, no overflow): q = RN(1/b0), whose residual 1 - q b0 is a
+// double (exact by FMA), then 1/b = q / (1 - r) with r = 1 - q b, |r| <=
+// 2^-52, taken as q (1 + r + r^2); relative error below 2^-103.
+MD_INLINE md<2> dd_recip(const md<2>& b) {
+    const double q = 1.0 / b.v[0];
+    const double r = dfma(-q, b.v[1], dfma(-q, b.v[0], 1.0));
+    return dd_fast_sum(q, dmul(q, dfma(r, r, r)));
+}
+
+// sqrt(a) for a0 > 0: s = RN(sqrt(a0)), whose residual a0 - s^2 is a double
+// (exact by FMA); sqrt(a) = s sqrt(1 + t) with t = (a - s^2) / s^2, |t| <=
+// 2^-51, taken as s + (a - s^2) / (2 s); relative error below 2^-103.
+MD_INLINE md<2> dd_sqrt(const md<2>& a) {
+    const double s = sqrt(a.v[0]);
+    const double y = 1.0 / s;
+    const double r = dadd(dfma(-s, s, a.v[0]), a.v[1]);
+    return dd_fast_sum(s, dmul(dmul(r, y), 0.5));
+}
+
+// The Householder scalars of xf_house from sig > 0 (the squared norm below
+// the diagonal) and x0 in double double: mu = sqrt(x0^2 + sig),
+// v0 = x0 - mu (x0 <= 0) or -sig / (x0 + mu) (x0 > 0, no cancellation),
+// inv = 1/v0, bp = -1/(mu v0) = -inv/mu, beta = bp v0^2 = -v0/mu.  The
+// chain: mu, then one addition, one reciprocal and one product each way;
+// 1/mu and 1/sig are formed beside it.
+MD_INLINE void house_dd(const md<2>& sig, const md<2>& x0, md<2>& mu, md<2>& v0, md<2>& bp, md<2>& inv,
+                        md<2>& beta) {
+    const md<2> rsig = dd_recip(sig);
+    mu = dd_sqrt(md_add<2>(sig, dd_mul(x0, x0)));
+    const md<2> rmu = dd_recip(mu);
+    if (x0.v[0] <= 0.0) {
+        v0 = md_sub<2>(x0, mu);
+        inv = dd_recip(v0);
+    } else {
+        const md<2> sx = md_add<2>(x0, mu);
+        v0 = md_neg<2>(dd_mul(sig, dd_recip(sx)));
+        inv = md_neg<2>(dd_mul(sx, rsig));
+    }
+    bp = md_neg<2>(dd_mul(rmu, inv));
+    beta = md_neg<2>(dd_mul(v0, rmu));
+}
+
+// house_dd between digit scalars, one thread: the form the host replay and
+// the tests use (the panels run house_dd with the conversions spread over a
+// warp and get the same digits).  Kinds and degenerate cases as xf_house.
+template <int N>
+FX_CALL int xf_house_dd(const xf<N>& sig_x, const xf<N>& x0_x, xf<N>& v0, xf<N>& bp, xf<N>& rcc, xf<N>& inv_v0,
+                        xf<N>& beta) {
+    if (xf_is_zero(sig_x)) return xf_house_md<2, N>(sig_x, x0_x, v0, bp, rcc, inv_v0, beta);
+    md<2> mu, v0m, bpm, invm, betam;
+    house_dd(xf_to_md<2, N>(sig_x), xf_to_md<2, N>(x0_x), mu, v0m, bpm, invm, betam);
+    v0 = xf_from_md<2, N>(v0m);
+    bp = xf_from_md<2, N>(bpm);
+    inv_v0 = xf_from_md<2, N>(invm);
+    beta = xf_from_md<2, N>(betam);
+    rcc = xf_from_md<2, N>(mu);
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
 // Panel entries (fixed point with a per-column digit scale e)
 // ---------------------------------------------------------------------------
 

@@ -173,51 +173,66 @@ __device__ __forceinline__ double lead(const wxf& x, int& k) {
            (double)digit(x, N - 3);
 }
 
-// fx::xf_from_double: the lane's entry of fx::add_double<6> into zeros.
-template <int N>
-__device__ __forceinline__ wxf from_double(double v) {
+// The lane's entry of fx::add_double<n>(c, v, e) into zeros: digit k of v at
+// digit scale e (bits below 2^(24e) truncated), 0 in lanes >= n.
+template <int n>
+__device__ __forceinline__ int64_t double_part(double v, int e) {
     uint64_t u = fx::dbits(v);
     const bool negv = (u >> 63) != 0;
     u &= 0x7fffffffffffffffULL;
-    if (u == 0) return zero();
-    const int msb = fx::dmsb(v);
-    const int e = fx::floordiv24(msb) - 3;
-    int64_t mine = 0;
-    if ((u >> 52) != 0x7ff) {
-        const int be = (int)(u >> 52);
-        uint64_t m = u & ((uint64_t(1) << 52) - 1);
-        int L;
-        if (be == 0) {
-            L = -1074;
-        } else {
-            m |= uint64_t(1) << 52;
-            L = be - 1075;
-        }
-        int p = L - kB * e;
-        bool keep = true;
-        if (p < 0) {
-            if (p <= -64) keep = false;
-            else m >>= -p;
-            p = 0;
-        }
-        if (keep) {
-            const int q = p / kB, b = p % kB;
-            const int64_t lo = (int64_t)((m & (uint64_t)kMask) << b);
-            const int64_t hi = (int64_t)((m >> kB) << b);
-            int64_t t0 = lo & kMask, t1 = (lo >> kB) + (hi & kMask), t2 = hi >> kB;
-            if (negv) {
-                t0 = -t0;
-                t1 = -t1;
-                t2 = -t2;
-            }
-            const int k = lane_id();
-            if (k < 6) {
-                if (k == q) mine += t0;
-                if (k == q + 1) mine += t1;
-                if (k == q + 2) mine += t2;
-            }
-        }
+    if (u == 0 || (u >> 52) == 0x7ff) return 0;
+    const int be = (int)(u >> 52);
+    uint64_t m = u & ((uint64_t(1) << 52) - 1);
+    int L;
+    if (be == 0) {
+        L = -1074;
+    } else {
+        m |= uint64_t(1) << 52;
+        L = be - 1075;
     }
+    int p = L - kB * e;
+    if (p < 0) {
+        if (p <= -64) return 0;
+        m >>= -p;
+        p = 0;
+    }
+    const int q = p / kB, b = p % kB;
+    const int64_t lo = (int64_t)((m & (uint64_t)kMask) << b);
+    const int64_t hi = (int64_t)((m >> kB) << b);
+    int64_t t = 0;
+    const int k = lane_id();
+    if (k < n) {
+        if (k == q) t = lo & kMask;
+        if (k == q + 1) t = (lo >> kB) + (hi & kMask);
+        if (k == q + 2) t = hi >> kB;
+    }
+    return negv ? -t : t;
+}
+
+// fx::xf_from_double
+template <int N>
+__device__ __forceinline__ wxf from_double(double v) {
+    if ((fx::dbits(v) & 0x7fffffffffffffffULL) == 0) return zero();
+    const int e = fx::floordiv24(fx::dmsb(v)) - 3;
+    return from_acc<N, N + 2>(double_part<6>(v, e), e);
+}
+
+// fx::xf_from_md: every limb at the digit scale that puts the leading bit in
+// digit N-1, summed by lanes, carried once.
+template <int P, int N>
+__device__ __forceinline__ wxf from_md(const md<P>& x) {
+    int msb = -100000;
+#pragma unroll
+    for (int l = 0; l < P; ++l)
+        if ((fx::dbits(x.v[l]) & 0x7fffffffffffffffULL) != 0) {
+            const int m = fx::dmsb(x.v[l]);
+            msb = m > msb ? m : msb;
+        }
+    if (msb == -100000) return zero();
+    const int e = fx::floordiv24(msb) - (N - 1);
+    int64_t mine = 0;
+#pragma unroll
+    for (int l = 0; l < P; ++l) mine += double_part<N + 2>(x.v[l], e);
     return from_acc<N, N + 2>(mine, e);
 }
 

@@ -84,26 +84,66 @@ DEV_INLINE void block_digit_sum(int64_t (&acc)[M], int64_t (*red)[M]) {
     __syncthreads();
 }
 
-// The reflector's scalars for one warp: in double-double FP64 arithmetic
-// for P = 2 (fx::xf_house_md: a few hundred FP64 instructions, every lane
-// computing the same values; 5x fewer cycles than the digit Newton steps),
-// in digits spread over the warp for quad and octo double, whose P-limb
-// divisions and square roots cost more than the digit Newton steps.
+// The reflector's scalars on one warp, in two steps: panel_house_lead forms
+// what the other columns wait for (the kind, v0 and bp in digits),
+// panel_house_tail the rest (1/v0 in digits for the vector; R_cc and beta in
+// P limbs).  Double double runs fx::house_dd on the FP64 pipe, every lane
+// computing the same values, with the digit conversions spread over lanes;
+// quad and octo double run the digit Newton steps spread over the warp,
+// which cost less than their P-limb divisions and square roots.
 template <int P, int N>
-DEV_INLINE int panel_house(const fxw::wxf& sig, const fxw::wxf& x0, fxw::wxf& v0, fxw::wxf& bp, fxw::wxf& rcc,
-                           fxw::wxf& inv, fxw::wxf& bet) {
+struct PanelHouse {
+    int kind;
+    fxw::wxf v0, bp, inv;   // digits: published v0 and bp; 1/v0 for the vector
+    md<P> rcc, beta;        // R_cc and beta (every lane) after the tail
+    fxw::wxf rcc_w, bet_w;  // their digit forms until the tail (P > 2)
+    md<P> invm;             // 1/v0 in P limbs until the tail (P = 2, kind 0)
+};
+
+template <int P, int N>
+DEV_INLINE void panel_house_lead(const fxw::wxf& sig, const fxw::wxf& x0, PanelHouse<P, N>& h) {
     if constexpr (P == 2) {
         const fx::xf<N> s = fxw::to_scalar<N>(sig), x = fxw::to_scalar<N>(x0);
-        fx::xf<N> a, b, c, d, e;
-        const int kind = fx::xf_house_md<P, N>(s, x, a, b, c, d, e);
-        v0 = fxw::from_scalar<N>(a);
-        bp = fxw::from_scalar<N>(b);
-        rcc = fxw::from_scalar<N>(c);
-        inv = fxw::from_scalar<N>(d);
-        bet = fxw::from_scalar<N>(e);
-        return kind;
+        if (fx::xf_is_zero<N>(s)) {  // kinds 1 and 2: no reflection or a sign flip
+            fx::xf<N> a, b, c, d, e;
+            h.kind = fx::xf_house_md<P, N>(s, x, a, b, c, d, e);
+            h.v0 = fxw::from_scalar<N>(a);
+            h.bp = fxw::from_scalar<N>(b);
+            h.inv = fxw::from_scalar<N>(d);
+            h.rcc = fx::xf_to_md<P, N>(c);
+            h.beta = fx::xf_to_md<P, N>(e);
+            return;
+        }
+        // lane 1 rounds x0 to double double, the other lanes sig
+        const int lane = threadIdx.x & 31;
+        fx::xf<N> in;
+#pragma unroll
+        for (int k = 0; k < N; ++k) in.d[k] = lane == 1 ? x.d[k] : s.d[k];
+        in.e = lane == 1 ? x.e : s.e;
+        const md<P> m = fx::xf_to_md<P, N>(in);
+        md<P> sm, xm, v0m, bpm;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            sm.v[l] = __shfl_sync(0xffffffffu, m.v[l], 0);
+            xm.v[l] = __shfl_sync(0xffffffffu, m.v[l], 1);
+        }
+        fx::house_dd(sm, xm, h.rcc, v0m, bpm, h.invm, h.beta);
+        h.kind = 0;
+        h.v0 = fxw::from_md<P, N>(v0m);
+        h.bp = fxw::from_md<P, N>(bpm);
     } else {
-        return fxw::house<N>(sig, x0, v0, bp, rcc, inv, bet);
+        h.kind = fxw::house<N>(sig, x0, h.v0, h.bp, h.rcc_w, h.inv, h.bet_w);
+    }
+}
+
+template <int P, int N>
+DEV_INLINE void panel_house_tail(PanelHouse<P, N>& h) {
+    if constexpr (P == 2) {
+        if (h.kind == 0) h.inv = fxw::from_md<P, N>(h.invm);
+    } else {
+        const fx::xf<N> bet_s = fxw::to_scalar<N>(h.bet_w), rcc_s = fxw::to_scalar<N>(h.rcc_w);
+        h.beta = fx::xf_to_md<P, N>(bet_s);
+        h.rcc = fx::xf_to_md<P, N>(rcc_s);
     }
 }
 
@@ -295,24 +335,24 @@ __global__ void __launch_bounds__(NT, 2) fx_panel_kernel(FxPanelArgs a) {
         const int64_t tot = lane < M ? red[0][lane] : 0;
         const fxw::wxf sig = fxw::from_acc<N, M>(tot, 2 * ec + D - 3);
         const int32_t xe = lane < D ? Fc[lane * fs + c] : 0;
-        fxw::wxf v0, bp, rcc, inv, bet;
-        const int kind = panel_house<P, N>(sig, fxw::from_fixed<N, D>(xe, ec), v0, bp, rcc, inv, bet);
-        if (lane == 0) Mc[FxMeta<P>::kKind] = kind;
-        wst_xf<N>(Mc + FxMeta<P>::kV0, v0);
-        wst_xf<N>(Mc + FxMeta<P>::kBp, bp);
+        PanelHouse<P, N> h;
+        panel_house_lead<P, N>(sig, fxw::from_fixed<N, D>(xe, ec), h);
+        if (lane == 0) Mc[FxMeta<P>::kKind] = h.kind;
+        wst_xf<N>(Mc + FxMeta<P>::kV0, h.v0);
+        wst_xf<N>(Mc + FxMeta<P>::kBp, h.bp);
         __syncwarp();
         if (lane == 0) {
             __threadfence();
             atomicExch(a.flags + a.w + c, a.epoch);
         }
         // outputs: beta, R_cc; 1/v0 for the vector
-        const xf<N> bet_s = fxw::to_scalar<N>(bet), rcc_s = fxw::to_scalar<N>(rcc);
+        panel_house_tail<P, N>(h);
         if (lane == 0) {
-            st_md<P>(a.beta, a.beta_ps, c, finite ? xf_to_md<P, N>(bet_s) : md_from_double<P>(dnan()));
-            st_md<P>(colc, ps, c, finite ? xf_to_md<P, N>(rcc_s) : md_from_double<P>(dnan()));
+            st_md<P>(a.beta, a.beta_ps, c, finite ? h.beta : md_from_double<P>(dnan()));
+            st_md<P>(colc, ps, c, finite ? h.rcc : md_from_double<P>(dnan()));
         }
-        if (lane < N) sh_x[lane] = inv.d;
-        if (lane == 0) sh_x[N] = inv.e;
+        if (lane < N) sh_x[lane] = h.inv.d;
+        if (lane == 0) sh_x[N] = h.inv.e;
     } else {
         if (qsh > 0) {
             for (int64_t i = c + 1 + (tid - 32); i < r; i += NT - 32) {
@@ -484,25 +524,23 @@ __global__ void __launch_bounds__(NT) fx_panel_block_kernel(FxBlockPanelArgs a) 
             const int64_t tot = lane < M ? red[0][lane] : 0;
             const fxw::wxf sig = fxw::from_acc<N, M>(tot, 2 * ec + D - 3);
             const int32_t xe = lane < D ? Fc[lane * fs + c] : 0;
-            fxw::wxf v0, bp, rcc, inv, bet;
-            const int kind = panel_house<P, N>(sig, fxw::from_fixed<N, D>(xe, ec), v0, bp, rcc, inv, bet);
+            PanelHouse<P, N> h;
+            panel_house_lead<P, N>(sig, fxw::from_fixed<N, D>(xe, ec), h);
+            panel_house_tail<P, N>(h);
             if (lane < N) {
-                sh_v0[lane] = v0.d;
-                sh_bp[lane] = bp.d;
-                sh_inv[c][lane] = inv.d;
+                sh_v0[lane] = h.v0.d;
+                sh_bp[lane] = h.bp.d;
+                sh_inv[c][lane] = h.inv.d;
             }
             if (lane == 0) {
-                sh_v0[N] = v0.e;
-                sh_bp[N] = bp.e;
-                sh_inv[c][N] = inv.e;
-                sh_kind[c] = kind;
+                sh_v0[N] = h.v0.e;
+                sh_bp[N] = h.bp.e;
+                sh_inv[c][N] = h.inv.e;
+                sh_kind[c] = h.kind;
                 sh_eu[c] = eu;
-            }
-            const xf<N> bet_s = fxw::to_scalar<N>(bet), rcc_s = fxw::to_scalar<N>(rcc);
-            if (lane == 0) {
                 const bool fin = sh_fin[c] != 0;
-                st_md<P>(a.beta, a.beta_ps, c, fin ? xf_to_md<P, N>(bet_s) : md_from_double<P>(dnan()));
-                st_md<P>(base + (int64_t)c * a.ld, ps, c, fin ? xf_to_md<P, N>(rcc_s) : md_from_double<P>(dnan()));
+                st_md<P>(a.beta, a.beta_ps, c, fin ? h.beta : md_from_double<P>(dnan()));
+                st_md<P>(base + (int64_t)c * a.ld, ps, c, fin ? h.rcc : md_from_double<P>(dnan()));
             }
         } else if (qsh > 0) {
             for (int64_t i = c + 1 + (tid - 32); i < r; i += NT - 32) {

@@ -129,15 +129,18 @@ extern "C" int fx_axpy(int p, long n, double* a, const double* u, const double* 
 
 // Householder scalars from sigma and x0 (entries i): v0, bp, R, 1/v0, beta
 // and the kind.
-// md_variant: the P-limb FP64 form (xf_house_md) instead of the digit form.
+// variant 0: digits (xf_house); 1: the P-limb FP64 form (xf_house_md);
+// 2: the short-chain double double form the panels run (xf_house_dd, P = 2).
 template <int P>
 static void house(long n, const double* sig, const double* x0, double* v0, double* bp, double* rcc,
-                  double* inv, double* beta, int* kind, bool md_variant) {
+                  double* inv, double* beta, int* kind, int variant) {
     constexpr int N = Cfg<P>::N;
     for (long i = 0; i < n; ++i) {
         xf<N> V, B, R, I, Be;
         const xf<N> S = xf_from_md<P, N>(load<P>(sig, n, i)), X = xf_from_md<P, N>(load<P>(x0, n, i));
-        kind[i] = md_variant ? xf_house_md<P, N>(S, X, V, B, R, I, Be) : xf_house<N>(S, X, V, B, R, I, Be);
+        kind[i] = variant == 2   ? xf_house_dd<N>(S, X, V, B, R, I, Be)
+                  : variant == 1 ? xf_house_md<P, N>(S, X, V, B, R, I, Be)
+                                 : xf_house<N>(S, X, V, B, R, I, Be);
         store<P>(v0, n, i, xf_to_md<P, N>(V));
         store<P>(bp, n, i, xf_to_md<P, N>(B));
         store<P>(rcc, n, i, xf_to_md<P, N>(R));
@@ -148,16 +151,22 @@ static void house(long n, const double* sig, const double* x0, double* v0, doubl
 
 extern "C" void fx_house(int p, long n, const double* sig, const double* x0, double* v0, double* bp,
                          double* rcc, double* inv, double* beta, int* kind) {
-    if (p == 2) house<2>(n, sig, x0, v0, bp, rcc, inv, beta, kind, false);
-    else if (p == 4) house<4>(n, sig, x0, v0, bp, rcc, inv, beta, kind, false);
-    else house<8>(n, sig, x0, v0, bp, rcc, inv, beta, kind, false);
+    if (p == 2) house<2>(n, sig, x0, v0, bp, rcc, inv, beta, kind, 0);
+    else if (p == 4) house<4>(n, sig, x0, v0, bp, rcc, inv, beta, kind, 0);
+    else house<8>(n, sig, x0, v0, bp, rcc, inv, beta, kind, 0);
 }
 
 extern "C" void fx_house_md(int p, long n, const double* sig, const double* x0, double* v0, double* bp,
                             double* rcc, double* inv, double* beta, int* kind) {
-    if (p == 2) house<2>(n, sig, x0, v0, bp, rcc, inv, beta, kind, true);
-    else if (p == 4) house<4>(n, sig, x0, v0, bp, rcc, inv, beta, kind, true);
-    else house<8>(n, sig, x0, v0, bp, rcc, inv, beta, kind, true);
+    if (p == 2) house<2>(n, sig, x0, v0, bp, rcc, inv, beta, kind, 1);
+    else if (p == 4) house<4>(n, sig, x0, v0, bp, rcc, inv, beta, kind, 1);
+    else house<8>(n, sig, x0, v0, bp, rcc, inv, beta, kind, 1);
+}
+
+// double double only
+extern "C" void fx_house_dd(long n, const double* sig, const double* x0, double* v0, double* bp, double* rcc,
+                            double* inv, double* beta, int* kind) {
+    house<2>(n, sig, x0, v0, bp, rcc, inv, beta, kind, 2);
 }
 
 // Sequential replay of the integer-digit panel (one panel of all n columns
@@ -246,8 +255,8 @@ static int panel_replay(long m, long n, double* A, double* beta) {
         xf<N> v0, bp, rcc, inv, bet;
         // as on the GPU: double-double FP64 scalars for P = 2, digits otherwise
         const xf<N> sig_x = xf_from_acc<N>(sacc, 2 * ec + D - 3), x0_x = xf_from_fixed<N, D>(xe, ec);
-        kinds[c] = P == 2 ? xf_house_md<P, N>(sig_x, x0_x, v0, bp, rcc, inv, bet)
-                          : xf_house<N>(sig_x, x0_x, v0, bp, rcc, inv, bet);
+        if constexpr (P == 2) kinds[c] = xf_house_dd<N>(sig_x, x0_x, v0, bp, rcc, inv, bet);
+        else kinds[c] = xf_house<N>(sig_x, x0_x, v0, bp, rcc, inv, bet);
         v0s[c] = v0;
         bps[c] = bp;
         store<P>(beta, n, c, xf_to_md<P, N>(bet));

@@ -4,7 +4,7 @@
 // same inputs in every lane) and the two results must agree exactly.
 #include <cstdint>
 
-#include "../../paper_2110_08375_gb300/csrc/fxw.cuh"
+#include "../../paper_2110_08375_gb300/csrc/panel_fx.cuh"
 
 using namespace mdls;
 
@@ -45,10 +45,28 @@ __device__ bool same(const fx::xf<N>& s, const fxw::wxf& w) {
     return ok;
 }
 
+template <int N>
+__device__ bool same_xf(const fx::xf<N>& a, const fx::xf<N>& b) {
+    bool ok = a.e == b.e || (fx::xf_is_zero<N>(a) && fx::xf_is_zero<N>(b));
+    for (int k = 0; k < N; ++k) ok = ok && a.d[k] == b.d[k];
+    return ok;
+}
+
+template <int P>
+__device__ bool same_md(const md<P>& a, const md<P>& b) {
+    bool ok = true;
+    for (int l = 0; l < P; ++l) ok = ok && fx::dbits(a.v[l]) == fx::dbits(b.v[l]);
+    return ok;
+}
+
 // bad[op] counts the cases where op differs; ops: 0 mul, 1 add, 2 sub,
 // 3 recip, 4 rsqrt, 5 house (all outputs and the kind), 6 from_double,
-// 7 fixed round trip, 8 shift_bits, 9 from_acc of a wide accumulator
-template <int N, int D>
+// 7 fixed round trip, 8 shift_bits, 9 from_acc of a wide accumulator,
+// 10 from_md, 11 the panels' two-step scalars (panel_house_lead and _tail)
+// against the one-thread form (xf_house_dd for P = 2, else xf_house)
+constexpr int kOps = 12;
+
+template <int P, int N, int D>
 __global__ void check_kernel(int cases, uint64_t seed, int* bad) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= cases) return;  // whole warp
@@ -60,7 +78,7 @@ __global__ void check_kernel(int cases, uint64_t seed, int* bad) {
     if (w % 7 == 2) b.e = a.e + (int)(mix64(key + 2) % 5) - 2;  // overlapping windows, cancellation
     if (w % 11 == 4) b = fx::xf_neg<N>(a);
     const fxw::wxf wa = fxw::from_scalar<N>(a), wb = fxw::from_scalar<N>(b);
-    bool ok[10];
+    bool ok[kOps];
     ok[0] = same<N>(fx::xf_mul<N>(a, b), fxw::mul<N>(wa, wb));
     ok[1] = same<N>(fx::xf_add<N>(a, b), fxw::add<N>(wa, wb));
     ok[2] = same<N>(fx::xf_sub<N>(a, b), fxw::sub<N>(wa, wb));
@@ -113,8 +131,45 @@ __global__ void check_kernel(int cases, uint64_t seed, int* bad) {
         const int64_t mine = lane < M ? c[lane] : 0;
         ok[9] = same<N>(fx::xf_from_acc<N, M>(c, -3), fxw::from_acc<N, M>(mine, -3));
     }
+    {
+        // P limbs, each about 2^-53 below the previous, some zero or tiny
+        md<P> x;
+        const uint64_t r0 = mix64(key + 7);
+        double v = ldexp((double)(int64_t)(r0 >> 11) * 0x1p-53, (int)((r0 >> 3) % 120) - 60);
+        for (int l = 0; l < P; ++l) {
+            const uint64_t r = mix64(key * 5 + 200 + l);
+            x.v[l] = (r & 15) == 0 ? 0.0 : v;
+            v = v * 0x1p-53 * ((double)(int64_t)(r >> 11) * 0x1p-52) * ((r & 16) ? 1.0 : 0x1p-30);
+        }
+        if (w % 23 == 7) x = md_zero<P>();
+        ok[10] = same<N>(fx::xf_from_md<P, N>(x), fxw::from_md<P, N>(x));
+    }
+    {
+        // magnitudes within the double range (leading digit at 2^(24e), |e| <= 20)
+        fx::xf<N> sig = (w % 13 == 6) ? fx::xf_zero<N>() : pa, x0 = b;
+        if (!fx::xf_is_zero<N>(sig)) sig.e -= N - 1;
+        if (!fx::xf_is_zero<N>(x0)) x0.e -= N - 1;
+        fx::xf<N> v0, bp, rcc, inv, bet;
+        int kind;
+        if constexpr (P == 2) kind = fx::xf_house_dd<N>(sig, x0, v0, bp, rcc, inv, bet);
+        else kind = fx::xf_house<N>(sig, x0, v0, bp, rcc, inv, bet);
+        PanelHouse<P, N> h;
+        panel_house_lead<P, N>(fxw::from_scalar<N>(sig), fxw::from_scalar<N>(x0), h);
+        const bool lead_ok = h.kind == kind && same<N>(v0, h.v0) && same<N>(bp, h.bp);
+        panel_house_tail<P, N>(h);
+        bool tail_ok = same<N>(inv, h.inv);
+        if (P == 2 && kind == 0) {
+            // the panels keep R_cc and beta in limbs; the one-thread form
+            // rounds them to digits
+            tail_ok = tail_ok && same_xf<N>(rcc, fx::xf_from_md<P, N>(h.rcc)) &&
+                      same_xf<N>(bet, fx::xf_from_md<P, N>(h.beta));
+        } else {
+            tail_ok = tail_ok && same_md<P>(fx::xf_to_md<P, N>(rcc), h.rcc) && same_md<P>(fx::xf_to_md<P, N>(bet), h.beta);
+        }
+        ok[11] = lead_ok && tail_ok;
+    }
     if (lane == 0)
-        for (int q = 0; q < 10; ++q)
+        for (int q = 0; q < kOps; ++q)
             if (!ok[q]) atomicAdd(bad + q, 1);
 }
 
@@ -122,14 +177,14 @@ template <int P>
 int run(int cases, uint64_t seed, int* host_bad) {
     constexpr int N = fx::Cfg<P>::N, D = fx::Cfg<P>::D;
     int* bad = nullptr;
-    if (cudaMalloc(&bad, 10 * sizeof(int)) != cudaSuccess) return -1;
-    cudaMemset(bad, 0, 10 * sizeof(int));
-    check_kernel<N, D><<<(cases + 3) / 4, 128>>>(cases, seed, bad);
+    if (cudaMalloc(&bad, kOps * sizeof(int)) != cudaSuccess) return -1;
+    cudaMemset(bad, 0, kOps * sizeof(int));
+    check_kernel<P, N, D><<<(cases + 3) / 4, 128>>>(cases, seed, bad);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         cudaFree(bad);
         return -2;
     }
-    cudaMemcpy(host_bad, bad, 10 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpy(host_bad, bad, kOps * sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(bad);
     return 0;
 }

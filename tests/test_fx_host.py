@@ -44,6 +44,7 @@ def fx():
     L.fx_axpy.restype = C.c_int
     L.fx_house.argtypes = [C.c_int, C.c_long, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_int)]
     L.fx_house_md.argtypes = [C.c_int, C.c_long, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_int)]
+    L.fx_house_dd.argtypes = [C.c_long, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_int)]
     L.fx_panel_replay.argtypes = [C.c_int, C.c_long, C.c_long, dp, dp]
     L.dp, L.ip = dp, ip
     return L
@@ -235,15 +236,16 @@ def test_update_refuses_a_multiplier_that_does_not_fit(fx):
                       w.ctypes.data_as(fx.dp), -(d - 1), -(d - 1)) == 0
 
 
-@pytest.mark.parametrize("p", PS)
-@pytest.mark.parametrize("variant", ["digits", "md"])
+@pytest.mark.parametrize("p,variant", [(p, v) for p in PS for v in ("digits", "md")] + [(2, "dd")])
 def test_householder_scalars(fx, p, variant):
     """Golub and Van Loan's house() with the unscaled vector: mu = sqrt(x0^2 +
     sigma), v0 = x0 - mu, bp = -1/(mu v0) = 2/||u||^2, beta = bp v0^2, 1/v0;
-    and the two degenerate kinds for sigma = 0.  Both forms: Newton on
-    digits (within a few units of 2^(-53P)), and P-limb FP64 arithmetic
+    and the two degenerate kinds for sigma = 0.  Three forms: Newton on
+    digits (within a few units of 2^(-53P)), P-limb FP64 arithmetic
     (xf_house_md, within 2^(10-53P): a handful of md operations, each with a
-    relative error of a few units of 2^(-53P))."""
+    relative error of a few units of 2^(-53P)), and the short-chain double
+    double form of the panels (xf_house_dd: Newton-corrected reciprocals and
+    root, products, the same bound)."""
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.prec = 53 * p + 200
     rng = np.random.default_rng(11)
@@ -257,9 +259,12 @@ def test_householder_scalars(fx, p, variant):
     x0[:, 5] = 0.0                                       # x0 = 0 with sigma > 0
     outs = [np.zeros((p, n)) for _ in range(5)]
     kind = np.zeros(n, dtype=np.int32)
-    fn = fx.fx_house if variant == "digits" else fx.fx_house_md
-    fn(p, n, sig.ctypes.data_as(fx.dp), x0.ctypes.data_as(fx.dp),
-       *[o.ctypes.data_as(fx.dp) for o in outs], kind.ctypes.data_as(C.POINTER(C.c_int)))
+    args = [sig.ctypes.data_as(fx.dp), x0.ctypes.data_as(fx.dp),
+            *[o.ctypes.data_as(fx.dp) for o in outs], kind.ctypes.data_as(C.POINTER(C.c_int))]
+    if variant == "dd":
+        fx.fx_house_dd(n, *args)
+    else:
+        (fx.fx_house if variant == "digits" else fx.fx_house_md)(p, n, *args)
     v0, bp, rcc, inv, beta = outs
     mp = lambda x, i: mpmath.fsum([mpmath.mpf(float(v)) for v in x[:, i]])
     tol = mpmath.mpf(2) ** (-53 * p + (6 if variant == "digits" else 10))

@@ -4,7 +4,9 @@ against their one-thread namesakes of csrc/fx.cuh, digit for digit, on random
 sign-consistent inputs in every precision: products, sums with cancellation
 and disjoint windows, Newton reciprocals and inverse square roots, the three
 kinds of Householder scalars, conversions from doubles and to and from the
-fixed-point column format, bit shifts and wide dot-product accumulators.  The
+fixed-point column format, bit shifts and wide dot-product accumulators,
+multiple doubles to digits, and the panels' two-step Householder scalars
+(lanes sharing the double double conversions) against the one-thread forms.  The
 scalar routines are pinned to exact rational arithmetic by test_fx_host.py."""
 import ctypes as C
 import os
@@ -17,7 +19,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-OPS = ["mul", "add", "sub", "recip", "rsqrt", "house", "from_double", "fixed", "shift_bits", "from_acc"]
+OPS = ["mul", "add", "sub", "recip", "rsqrt", "house", "from_double", "fixed", "shift_bits", "from_acc",
+       "from_md", "panel_house"]
 
 
 @pytest.fixture(scope="module")
@@ -35,7 +38,7 @@ def fxw():
 
 @pytest.mark.parametrize("p", [2, 4, 8])
 def test_warp_digits_match_scalar(fxw, p):
-    bad = (C.c_int * 10)()
+    bad = (C.c_int * len(OPS))()
     rc = fxw.fxw_check(p, 6000, 1000 + p, bad)
     assert rc == 0
-    assert list(bad) == [0] * 10, dict(zip(OPS, list(bad)))
+    assert list(bad) == [0] * len(OPS), dict(zip(OPS, list(bad)))
