@@ -6,7 +6,7 @@
 // lives in P separate registers, never in an array in memory.
 //
 // Building blocks are the error-free transforms
-//   two_sum   (Knuth):  s + e == a + b exactly,
+//   two_sum   (Fast2Sum on operands ordered by exponent): s + e == a + b exactly,
 //   two_prod  (FMA):    p + e == a * b exactly (no underflow),
 // written with explicit round-to-nearest intrinsics so that the compiler can
 // neither contract nor reassociate them.
@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace mdls {
 
@@ -50,11 +51,30 @@ inline double dfma(double a, double b, double c) { return ::fma(a, b, c); }
 inline double dnan() { return __builtin_nan(""); }
 #endif
 
-// Knuth's TwoSum (6 flops): s = fl(a+b), e = (a+b) - s exactly.
+// High word of |x| (sign cleared): for finite x its order is the order of
+// the exponents, and equal words mean equal exponents.
+MD_INLINE uint32_t hi_abs(double x) {
+#ifdef __CUDA_ARCH__
+    return (uint32_t)__double2hiint(x) & 0x7fffffffu;
+#else
+    uint64_t u;
+    memcpy(&u, &x, 8);
+    return (uint32_t)(u >> 32) & 0x7fffffffu;
+#endif
+}
+
+// TwoSum: s = fl(a+b), e = (a+b) - s exactly.  Dekker's Fast2Sum (3 flops)
+// after ordering the operands by exponent, which is exact whenever the
+// first operand's exponent is not below the second's; the ordering is a
+// compare and two selects on the integer pipe, which has some 30 times the
+// FP64 pipe's throughput on this GPU, instead of the three extra flops of
+// Knuth's branch-free TwoSum.  s and e are unique, so both forms return
+// the same bits.
 MD_INLINE void two_sum(double a, double b, double& s, double& e) {
-    double x = dadd(a, b);
-    double bb = dsub(x, a);
-    e = dadd(dsub(a, dsub(x, bb)), dsub(b, bb));
+    const bool ab = hi_abs(a) >= hi_abs(b);
+    const double big = ab ? a : b, small = ab ? b : a;
+    const double x = dadd(big, small);
+    e = dsub(small, dsub(x, big));
     s = x;
 }
 

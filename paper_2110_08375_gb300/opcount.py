@@ -71,7 +71,7 @@ def lstsq_table1_flops(p: int, m: int, n: int) -> int:
 # ---------------------------------------------------------------------------
 # FP64 cost of one device md operation (csrc/md.cuh)
 # ---------------------------------------------------------------------------
-TWO_SUM = (6, 6)      # (instructions, flops)
+TWO_SUM = (3, 3)      # (instructions, flops): Fast2Sum, the operand order taken on the integer pipe
 TWO_PROD = (2, 3)     # DMUL + DFMA
 DFMA = (1, 2)
 DADD = (1, 1)

@@ -57,9 +57,11 @@ def test_leading_term():
 
 
 def test_device_fma_cost_structure():
-    # dd: two_prod + two_sum (order 0), 2 FMAs + 2 adds (order 1), one two_sum (renorm)
-    assert opcount.fma_cost(2) == (2 + 6 + 2 + 2 + 6, 3 + 6 + 4 + 2 + 6)
-    assert opcount.add_cost(2) == (6 + 2 + 6, 6 + 2 + 6)
+    # dd: two_prod + two_sum (order 0), 2 FMAs + 2 adds (order 1), one two_sum
+    # (renorm); a two_sum is Fast2Sum (3 FP64 operations) after an integer
+    # ordering of its operands
+    assert opcount.fma_cost(2) == (2 + 3 + 2 + 2 + 3, 3 + 3 + 4 + 2 + 3)
+    assert opcount.add_cost(2) == (3 + 2 + 3, 3 + 2 + 3)
     assert opcount.fma_cost(4)[0] < opcount.fma_cost(8)[0]
 
 
