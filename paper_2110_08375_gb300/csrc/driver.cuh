@@ -258,6 +258,30 @@ int panel_capacity() {
     return cap;
 }
 
+// Look-ahead: the next tile's panel runs on a high-priority side stream
+// beside the rest of this tile's trailing update (the panel is bound by the
+// latency of its column chain and leaves most of each SM's FP64 pipe to the
+// product).  One side stream and two events per host thread.
+struct LookAhead {
+    cudaStream_t hi = nullptr;
+    cudaEvent_t ready = nullptr, done = nullptr;
+    bool ok = false;
+};
+
+inline LookAhead& look_ahead() {
+    thread_local LookAhead la;
+    thread_local bool tried = false;
+    if (!tried) {
+        tried = true;
+        int least = 0, greatest = 0;
+        la.ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+                cudaStreamCreateWithPriority(&la.hi, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+                cudaEventCreateWithFlags(&la.ready, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&la.done, cudaEventDisableTiming) == cudaSuccess;
+    }
+    return la;
+}
+
 // Blocked Householder QR (Algorithm 2) of the m x n leading part of the
 // working matrix A (ld, ps); columns n .. n+nextra-1 of A are right-hand
 // sides that receive the same transformations (Q^T b).  Q (m x m) is formed
@@ -292,28 +316,55 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
     const int64_t ntiles = (n + t - 1) / t;
     const bool want_q = (Q != nullptr);
 
+    // 1. panel of tile k: Householder vectors, beta, R_kk.  One block per
+    //    column in integer digits with flags between them (cooperative
+    //    launch); the small problems of batched solves use the single-block
+    //    panel.
+    auto panel = [&](int64_t k, cudaStream_t s) -> int {
+        const int64_t j0 = k * t;
+        const int w = (int)((n - j0) < t ? (n - j0) : t);
+        const int64_t r = m - j0;
+        StageScope sc(ST_PANEL, s);
+        if (single_block) {
+            FxBlockPanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, fxF, hdr};
+            fx_panel_block_kernel<P, fx_block_threads<P>()><<<1, fx_block_threads<P>(), 0, s>>>(pa);
+            return cudaGetLastError() == cudaSuccess ? MDLS_OK : MDLS_ERR_CUDA;
+        }
+        if (w > panel_capacity<P>()) return MDLS_ERR_UNSUPPORTED;
+        FxPanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, fxF, fxmeta, flags, (unsigned int)(k + 1), hdr};
+        void* args[] = {&pa};
+        if (cudaLaunchCooperativeKernel((const void*)fx_panel_kernel<P, fx_panel_threads<P>()>, dim3(w),
+                                        dim3(fx_panel_threads<P>()), args, 0, s) != cudaSuccess)
+            return MDLS_ERR_CUDA;
+        return MDLS_OK;
+    };
+    // look-ahead only for the one-problem path outside graph capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    LookAhead* la = nullptr;
+    if (!single_block && cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone &&
+        look_ahead().ok)
+        la = &look_ahead();
+    bool panel_ahead = false;  // tile k's panel was launched on the side stream
+    // every return joins the side stream back into st
+    struct Join {
+        LookAhead* la;
+        cudaStream_t st;
+        const bool& pending;
+        ~Join() {
+            if (pending) cudaStreamWaitEvent(st, la->done, 0);
+        }
+    } join{la, st, panel_ahead};
+
     for (int64_t k = 0; k < ntiles; ++k) {
         const int64_t j0 = k * t;
         const int w = (int)((n - j0) < t ? (n - j0) : t);
         const int64_t r = m - j0;
-        // 1. panel: Householder vectors, beta, R_kk.  One block per column in
-        //    integer digits with flags between them (cooperative launch); the
-        //    small problems of batched solves use the single-block panel.
-        {
-            StageScope sc(ST_PANEL, st);
-            if (single_block) {
-                FxBlockPanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, fxF, hdr};
-                fx_panel_block_kernel<P, fx_block_threads<P>()><<<1, fx_block_threads<P>(), 0, st>>>(pa);
-                MDLS_LAUNCH_CHECK();
-            } else {
-                if (w > panel_capacity<P>()) return MDLS_ERR_UNSUPPORTED;
-                FxPanelArgs pa{A, lda, psa, j0, r, w, beta, (int64_t)t, fxF, fxmeta, flags,
-                               (unsigned int)(k + 1), hdr};
-                void* args[] = {&pa};
-                if (cudaLaunchCooperativeKernel((const void*)fx_panel_kernel<P, fx_panel_threads<P>()>, dim3(w),
-                                                dim3(fx_panel_threads<P>()), args, 0, st) != cudaSuccess)
-                    return MDLS_ERR_CUDA;
-            }
+        if (panel_ahead) {
+            if (cudaStreamWaitEvent(st, la->done, 0) != cudaSuccess) return MDLS_ERR_CUDA;
+            panel_ahead = false;
+        } else {
+            const int prc = panel(k, st);
+            if (prc) return prc;
         }
         const int64_t nc = n + nextra - (j0 + w);  // trailing columns incl. right-hand sides
         if (nc <= 0 && !want_q && !keep_w) continue;
@@ -335,14 +386,36 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
         double* Wk = (want_q || keep_w) ? (Wb + j0 * ldw + j0) : Wb;
         rc = launch_gemm<P>(ST_W, st, sb, r, w, w, Y, ViewUpper{T, t, tt2}, Dense{Wk, ldw, psw}, true, false);
         if (rc) return rc;
-        // 3. trailing update C := C + Y (W^T C)
+        // 3. trailing update C := C + Y (W^T C); with look-ahead first the
+        //    next tile's wn columns, then that tile's panel on the side
+        //    stream, then the other columns here
         if (nc > 0) {
+            const int64_t wn = (k + 1 < ntiles) ? ((n - j0 - w) < t ? (n - j0 - w) : t) : 0;
+            const int64_t nfirst = (la != nullptr && wn > 0 && nc > wn) ? wn : nc;
             double* Cp = A + (j0 + w) * lda + j0;
-            rc = launch_gemm<P>(ST_TRAIL, st, sb, w, nc, r, ViewDenseT{Wk, ldw, psw}, ViewDense{Cp, lda, psa},
+            rc = launch_gemm<P>(ST_TRAIL, st, sb, w, nfirst, r, ViewDenseT{Wk, ldw, psw}, ViewDense{Cp, lda, psa},
                                 Dense{X, t, psx}, false, false);
             if (rc) return rc;
-            rc = launch_gemm<P>(ST_TRAIL, st, sb, r, nc, w, Y, ViewDense{X, t, psx}, Dense{Cp, lda, psa}, false, true);
+            rc = launch_gemm<P>(ST_TRAIL, st, sb, r, nfirst, w, Y, ViewDense{X, t, psx}, Dense{Cp, lda, psa}, false,
+                                true);
             if (rc) return rc;
+            if (nfirst < nc) {
+                if (cudaEventRecord(la->ready, st) != cudaSuccess ||
+                    cudaStreamWaitEvent(la->hi, la->ready, 0) != cudaSuccess)
+                    return MDLS_ERR_CUDA;
+                const int prc = panel(k + 1, la->hi);
+                if (prc) return prc;
+                if (cudaEventRecord(la->done, la->hi) != cudaSuccess) return MDLS_ERR_CUDA;
+                panel_ahead = true;
+                double* Cq = Cp + nfirst * lda;
+                double* Xq = X + nfirst * t;
+                rc = launch_gemm<P>(ST_TRAIL, st, sb, w, nc - nfirst, r, ViewDenseT{Wk, ldw, psw},
+                                    ViewDense{Cq, lda, psa}, Dense{Xq, t, psx}, false, false);
+                if (rc) return rc;
+                rc = launch_gemm<P>(ST_TRAIL, st, sb, r, nc - nfirst, w, Y, ViewDense{Xq, t, psx},
+                                    Dense{Cq, lda, psa}, false, true);
+                if (rc) return rc;
+            }
         }
     }
     if (want_q) {
