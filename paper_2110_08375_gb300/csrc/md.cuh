@@ -6,7 +6,7 @@
 // lives in P separate registers, never in an array in memory.
 //
 // Building blocks are the error-free transforms
-//   two_sum   (Fast2Sum on operands ordered by exponent): s + e == a + b exactly,
+//   two_sum   (an FP64 addition, its error on the integer pipe): s + e == a + b exactly,
 //   two_prod  (FMA):    p + e == a * b exactly (no underflow),
 // written with explicit round-to-nearest intrinsics so that the compiler can
 // neither contract nor reassociate them.
@@ -51,31 +51,99 @@ inline double dfma(double a, double b, double c) { return ::fma(a, b, c); }
 inline double dnan() { return __builtin_nan(""); }
 #endif
 
-// High word of |x| (sign cleared): for finite x its order is the order of
-// the exponents, and equal words mean equal exponents.
-MD_INLINE uint32_t hi_abs(double x) {
+MD_INLINE uint64_t dbits64(double x) {
 #ifdef __CUDA_ARCH__
-    return (uint32_t)__double2hiint(x) & 0x7fffffffu;
+    return (uint64_t)__double_as_longlong(x);
 #else
     uint64_t u;
     memcpy(&u, &x, 8);
-    return (uint32_t)(u >> 32) & 0x7fffffffu;
+    return u;
 #endif
 }
 
-// TwoSum: s = fl(a+b), e = (a+b) - s exactly.  Dekker's Fast2Sum (3 flops)
-// after ordering the operands by exponent, which is exact whenever the
-// first operand's exponent is not below the second's; the ordering is a
-// compare and two selects on the integer pipe, which has some 30 times the
-// FP64 pipe's throughput on this GPU, instead of the three extra flops of
-// Knuth's branch-free TwoSum.  s and e are unique, so both forms return
-// the same bits.
-MD_INLINE void two_sum(double a, double b, double& s, double& e) {
-    const bool ab = hi_abs(a) >= hi_abs(b);
+MD_INLINE double dfrom64(uint64_t u) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double x;
+    memcpy(&x, &u, 8);
+    return x;
+#endif
+}
+
+// Signed significand m (two's complement) and exponent e of the last bit of
+// a finite double: x = m 2^e.
+MD_INLINE void sig_exp(uint64_t u, uint64_t& m, int& e) {
+    const int be = (int)((u >> 52) & 0x7ff);
+    const uint64_t mag = (u & 0xfffffffffffffULL) | ((uint64_t)(be != 0) << 52);
+    e = (be > 1 ? be : 1) - 1075;
+    m = (u >> 63) ? (uint64_t)0 - mag : mag;
+}
+
+MD_INLINE uint64_t shl_or_zero(uint64_t x, int k) { return k >= 64 ? 0 : x << k; }
+
+// The exact error (a + b) - s of s = fl(a + b), by integer arithmetic.  With
+// L the lowest last-bit exponent of a, b and s, the error is an integer
+// multiple of 2^L and below min(|a|, |b|) (or zero when s has the finest
+// last bit), so (a + b - s) / 2^L fits in 54 bits and is exact modulo 2^64
+// whatever the wrap-around of the shifted terms; it is then written out as
+// a double (exact: at most 53 significant bits).  The sign of a zero error
+// follows Fast2Sum's.  A non-finite s gives NaN.
+MD_INLINE double sum_error(double a, double b, double s) {
+    const uint64_t ua = dbits64(a), ub = dbits64(b), us = dbits64(s);
+    if (((us >> 52) & 0x7ff) == 0x7ff) return dfrom64(0x7ff8000000000000ULL);
+    uint64_t ma, mb, ms;
+    int ea, eb, es;
+    sig_exp(ua, ma, ea);
+    sig_exp(ub, mb, eb);
+    sig_exp(us, ms, es);
+    int L = ea < eb ? ea : eb;
+    L = L < es ? L : es;
+    const int64_t v = (int64_t)(shl_or_zero(ma, ea - L) + shl_or_zero(mb, eb - L) - shl_or_zero(ms, es - L));
+    constexpr uint64_t kNegZero = 0x8000000000000000ULL;
+    if (v == 0) return dfrom64((ub == kNegZero || (ua == kNegZero && ub != 0)) ? kNegZero : 0);
+    const uint64_t mag = v < 0 ? (uint64_t)0 - (uint64_t)v : (uint64_t)v;
+#ifdef __CUDA_ARCH__
+    const int n = 63 - __clzll((long long)mag);
+#else
+    const int n = 63 - __builtin_clzll(mag);
+#endif
+    const int E = n + L;  // exponent of the leading bit
+    uint64_t r = E >= -1022 ? (((uint64_t)(E + 1023) << 52) | ((mag << (52 - n)) & 0xfffffffffffffULL))
+                            : (mag << (L + 1074));
+    return dfrom64(r | ((uint64_t)(v < 0) << 63));
+}
+
+// TwoSum: s = fl(a+b), e = (a+b) - s exactly, in two forms with the same
+// bits (s and e are unique).  two_sum_int: s is one FP64 addition and e comes
+// from sum_error on the integer pipe, which has some 30 times the FP64 pipe's
+// throughput on this GPU.  two_sum_fast: Dekker's Fast2Sum (3 FP64
+// operations) after ordering the operands by exponent with an integer compare
+// of the sign-cleared high words; fewer registers.  Knuth's branch-free
+// TwoSum would take 6 FP64 operations.
+MD_INLINE void two_sum_int(double a, double b, double& s, double& e) {
+    const double x = dadd(a, b);
+    e = sum_error(a, b, x);
+    s = x;
+}
+
+MD_INLINE void two_sum_fast(double a, double b, double& s, double& e) {
+    const bool ab = (dbits64(a) << 1) >> 33 >= (dbits64(b) << 1) >> 33;
     const double big = ab ? a : b, small = ab ? b : a;
     const double x = dadd(big, small);
     e = dsub(small, dsub(x, big));
     s = x;
+}
+
+// The form bin D of a P-limb operation uses: the integer error for double
+// and quad double and the first four bins of octo double; the later od bins
+// carry up to 49 live error terms, and the integer form's temporaries there
+// would take the od product kernel from three blocks per SM to two (measured:
+// od slower by a quarter with the integer form everywhere).
+template <int P, int D>
+MD_INLINE void two_sum_pd(double a, double b, double& s, double& e) {
+    if constexpr (P <= 4 || D < 4) two_sum_int(a, b, s, e);
+    else two_sum_fast(a, b, s, e);
 }
 
 // TwoProd with FMA (2 flops): p = fl(ab), e = ab - p exactly.
@@ -128,7 +196,7 @@ MD_INLINE bool nonzero(double x) {
 template <int K, int P>
 MD_INLINE md<P> renorm_n(double (&s)[K]) {
 #pragma unroll
-    for (int i = K - 2; i >= 0; --i) two_sum(s[i], s[i + 1], s[i], s[i + 1]);
+    for (int i = K - 2; i >= 0; --i) two_sum_pd<P, P>(s[i], s[i + 1], s[i], s[i + 1]);
     md<P> y;
 #pragma unroll
     for (int k = 0; k < P; ++k) y.v[k] = 0.0;
@@ -137,7 +205,7 @@ MD_INLINE md<P> renorm_n(double (&s)[K]) {
 #pragma unroll
     for (int i = 1; i < K; ++i) {
         double r, e2;
-        two_sum(e, s[i], r, e2);
+        two_sum_pd<P, P>(e, s[i], r, e2);
         const bool emit = nonzero(e2);
 #pragma unroll
         for (int k = 0; k < P; ++k) y.v[k] = (emit && j == k) ? r : y.v[k];
@@ -183,7 +251,7 @@ struct FmaBin {
                 two_prod(a.v[i], b.v[D - i], hi, lo);
                 lo_cur[i] = lo;
                 if (have) {
-                    two_sum(acc, hi, acc, err_cur[ne]);
+                    two_sum_pd<P, D>(acc, hi, acc, err_cur[ne]);
                     ++ne;
                 } else {
                     acc = hi;
@@ -192,12 +260,12 @@ struct FmaBin {
             }
 #pragma unroll
             for (int i = 0; i < NLO; ++i) {
-                two_sum(acc, lo_prev[i], acc, err_cur[ne]);
+                two_sum_pd<P, D>(acc, lo_prev[i], acc, err_cur[ne]);
                 ++ne;
             }
 #pragma unroll
             for (int k = 0; k < NE; ++k) {
-                two_sum(acc, err_prev[k], acc, err_cur[ne]);
+                two_sum_pd<P, D>(acc, err_prev[k], acc, err_cur[ne]);
                 ++ne;
             }
             s[D] = acc;
@@ -278,9 +346,9 @@ struct AddBin {
         if constexpr (D < P - 1) {
             double err_cur[NOUT];
             double acc;
-            two_sum(a.v[D], b.v[D], acc, err_cur[0]);
+            two_sum_pd<P, D>(a.v[D], b.v[D], acc, err_cur[0]);
 #pragma unroll
-            for (int k = 0; k < NE; ++k) two_sum(acc, err_prev[k], acc, err_cur[k + 1]);
+            for (int k = 0; k < NE; ++k) two_sum_pd<P, D>(acc, err_prev[k], acc, err_cur[k + 1]);
             s[D] = acc;
             AddBin<P, D + 1, NOUT>::run(a, b, err_cur, s);
         } else {
@@ -316,15 +384,15 @@ struct FmaDBin {
             double err_cur[NOUT];
             double hi, lo, acc;
             two_prod(q, b.v[D], hi, lo);
-            two_sum(c.v[D], hi, acc, err_cur[0]);
+            two_sum_pd<P, D>(c.v[D], hi, acc, err_cur[0]);
             int ne = 1;
             if constexpr (D > 0) {
-                two_sum(acc, lo_prev, acc, err_cur[ne]);
+                two_sum_pd<P, D>(acc, lo_prev, acc, err_cur[ne]);
                 ++ne;
             }
 #pragma unroll
             for (int k = 0; k < NE; ++k) {
-                two_sum(acc, err_prev[k], acc, err_cur[ne]);
+                two_sum_pd<P, D>(acc, err_prev[k], acc, err_cur[ne]);
                 ++ne;
             }
             s[D] = acc;

@@ -71,7 +71,8 @@ def lstsq_table1_flops(p: int, m: int, n: int) -> int:
 # ---------------------------------------------------------------------------
 # FP64 cost of one device md operation (csrc/md.cuh)
 # ---------------------------------------------------------------------------
-TWO_SUM = (3, 3)      # (instructions, flops): Fast2Sum, the operand order taken on the integer pipe
+TWO_SUM_INT = (1, 1)   # (instructions, flops): the FP64 addition; its exact error on the integer pipe
+TWO_SUM_FAST = (3, 3)  # Fast2Sum, the operand order taken on the integer pipe
 TWO_PROD = (2, 3)     # DMUL + DFMA
 DFMA = (1, 2)
 DADD = (1, 1)
@@ -81,9 +82,17 @@ def _add(a, b, k=1):
     return (a[0] + k * b[0], a[1] + k * b[1])
 
 
+def two_sum_cost(p: int, d: int):
+    """The two_sum form bin d of a p-limb operation uses (csrc/md.cuh,
+    two_sum_pd): the integer error for p <= 4 and for the first four bins of
+    od; renormalisation counts as bin p."""
+    return TWO_SUM_INT if (p <= 4 or d < 4) else TWO_SUM_FAST
+
+
 def renorm_cost(p: int):
     n = (p - 1) + (p - 2 if p > 2 else 0)
-    return (n * TWO_SUM[0], n * TWO_SUM[1])
+    ts = two_sum_cost(p, p)
+    return (n * ts[0], n * ts[1])
 
 
 def fma_cost(p: int, with_c: bool = True):
@@ -95,7 +104,7 @@ def fma_cost(p: int, with_c: bool = True):
         if d < p - 1:
             nterms = (1 if with_c else 0) + (d + 1) + nlo + ne
             cost = _add(cost, TWO_PROD, d + 1)
-            cost = _add(cost, TWO_SUM, nterms - 1)
+            cost = _add(cost, two_sum_cost(p, d), nterms - 1)
             ne = nterms - 1
         else:
             cost = _add(cost, DFMA, d + 1)
@@ -116,7 +125,7 @@ def add_cost(p: int):
     ne = 0
     for d in range(p):
         if d < p - 1:
-            cost = _add(cost, TWO_SUM, 1 + ne)
+            cost = _add(cost, two_sum_cost(p, d), 1 + ne)
             ne += 1
         else:
             cost = _add(cost, DADD, 1 + ne)

@@ -33,3 +33,12 @@ extern "C" void md_host_op(int p, int op, long n, const double* a, const double*
     else if (p == 4) run<4>(op, n, a, b, c);
     else run<8>(op, n, a, b, c);
 }
+
+// two_sum in its two forms: 0 the integer error (two_sum_int), 1 Fast2Sum
+// after the integer ordering (two_sum_fast)
+extern "C" void md_host_two_sum(int form, long n, const double* a, const double* b, double* s, double* e) {
+    for (long i = 0; i < n; ++i) {
+        if (form == 0) two_sum_int(a[i], b[i], s[i], e[i]);
+        else two_sum_fast(a[i], b[i], s[i], e[i]);
+    }
+}

@@ -34,6 +34,7 @@ def harness():
     L = C.CDLL(out)
     dp = C.POINTER(C.c_double)
     L.md_host_op.argtypes = [C.c_int, C.c_int, C.c_long, dp, dp, dp]
+    L.md_host_two_sum.argtypes = [C.c_int, C.c_long, dp, dp, dp, dp]
 
     def run(p, op, a, b, c=None):
         a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
@@ -41,6 +42,7 @@ def harness():
         L.md_host_op(p, OPS[op], a.shape[1], a.ctypes.data_as(dp), b.ctypes.data_as(dp),
                      c.ctypes.data_as(dp))
         return c
+    run.lib, run.dp = L, dp
     return run
 
 
@@ -117,3 +119,63 @@ def test_far_apart_magnitudes(harness, p):
     b = draw(rng, p, n, -300, -150)
     for op in ("add", "sub", "mul", "div"):
         check(p, op, a, b, None, harness(p, op, a, b))
+
+
+def _two_sum_inputs(rng, n):
+    """Pairs that exercise every path of the error-free sum: mixed
+    magnitudes, near and exact cancellation, gaps beyond 53 bits and beyond
+    64, halfway cases (b = +-ulp(a)/2, 3 ulp(a)/2), subnormals, signed zeros
+    and magnitudes near overflow."""
+    def rnd(k, lo, hi):
+        m = 1.0 + rng.integers(0, 2 ** 52, k) * 2.0 ** -52
+        v = np.ldexp(m, rng.integers(lo, hi + 1, k))
+        return np.where(rng.integers(0, 2, k) == 1, -v, v)
+    k = n // 8
+    parts = []
+    parts.append((rnd(k, -30, 30), rnd(k, -30, 30)))
+    a = rnd(k, -5, 5)
+    parts.append((a, -a * (1 + rnd(k, -60, -40))))
+    parts.append((rnd(k, -1074, -1000), rnd(k, -1074, -1000)))
+    parts.append((rnd(k, -100, 100), rnd(k, -300, 300)))
+    a = rnd(k, -10, 10)
+    h = np.ldexp(1.0, np.frexp(a)[1] - 54)
+    parts.append((np.concatenate([a, a, a]), np.concatenate([h, -h, 3 * h])))
+    parts.append((rnd(k, 1000, 1022), rnd(k, 900, 1022)))
+    z = rnd(k, -20, 20)
+    zeros = np.array([0.0, -0.0])[rng.integers(0, 2, k)]
+    parts.append((np.concatenate([z, zeros, zeros]), np.concatenate([zeros, z, zeros[::-1]])))
+    bits = rng.integers(0, 2 ** 63, (2, k), dtype=np.int64).view(np.float64)
+    ok = np.isfinite(bits[0]) & np.isfinite(bits[1])
+    parts.append((bits[0][ok], bits[1][ok]))
+    a = np.concatenate([p[0] for p in parts] + [p[1] for p in parts])
+    b = np.concatenate([p[1] for p in parts] + [p[0] for p in parts])
+    return a, b
+
+
+def test_two_sum_forms_are_exact_and_agree(harness):
+    """Both two_sum forms give s = fl(a + b) and the exact error (Knuth's
+    TwoSum evaluated in numpy is the reference value), bit for bit the same
+    in either form, signed zeros included, for finite sums."""
+    rng = np.random.default_rng(7)
+    a, b = _two_sum_inputs(rng, 400000)
+    L, dp = harness.lib, harness.dp
+    out = {}
+    for form in (0, 1):
+        s = np.zeros_like(a)
+        e = np.zeros_like(a)
+        L.md_host_two_sum(form, a.size, a.ctypes.data_as(dp), b.ctypes.data_as(dp),
+                          s.ctypes.data_as(dp), e.ctypes.data_as(dp))
+        out[form] = (s, e)
+    with np.errstate(over="ignore", invalid="ignore"):
+        s_ref = a + b
+        bb = s_ref - a
+        e_ref = (a - (s_ref - bb)) + (b - bb)
+    fin = np.isfinite(s_ref)
+    assert fin.sum() > 0.95 * a.size
+    for form in (0, 1):
+        s, e = out[form]
+        assert np.array_equal(s[fin].view(np.int64), s_ref[fin].view(np.int64))
+        assert np.array_equal(e[fin], e_ref[fin])
+    assert np.array_equal(out[0][1][fin].view(np.int64), out[1][1][fin].view(np.int64))
+    # an overflowing sum gives a non-finite error in both forms
+    assert not np.isfinite(out[0][1][~fin]).any() and not np.isfinite(out[1][1][~fin]).any()

@@ -58,10 +58,10 @@ def test_leading_term():
 
 def test_device_fma_cost_structure():
     # dd: two_prod + two_sum (order 0), 2 FMAs + 2 adds (order 1), one two_sum
-    # (renorm); a two_sum is Fast2Sum (3 FP64 operations) after an integer
-    # ordering of its operands
-    assert opcount.fma_cost(2) == (2 + 3 + 2 + 2 + 3, 3 + 3 + 4 + 2 + 3)
-    assert opcount.add_cost(2) == (3 + 2 + 3, 3 + 2 + 3)
+    # (renorm); a two_sum is one FP64 addition, its error formed on the
+    # integer pipe
+    assert opcount.fma_cost(2) == (2 + 1 + 2 + 2 + 1, 3 + 1 + 4 + 2 + 1)
+    assert opcount.add_cost(2) == (1 + 2 + 1, 1 + 2 + 1)
     assert opcount.fma_cost(4)[0] < opcount.fma_cost(8)[0]
 
 
