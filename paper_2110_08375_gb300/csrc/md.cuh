@@ -136,13 +136,14 @@ MD_INLINE void two_sum_fast(double a, double b, double& s, double& e) {
 }
 
 // The form bin D of a P-limb operation uses: the integer error for double
-// and quad double and the first four bins of octo double; the later od bins
-// carry up to 49 live error terms, and the integer form's temporaries there
-// would take the od product kernel from three blocks per SM to two (measured:
-// od slower by a quarter with the integer form everywhere).
+// and quad double and the first five bins of octo double.  The later od bins
+// carry up to 49 live error terms: the integer form there takes the od
+// product kernel from three blocks per SM to two (od slower by a quarter),
+// and with it in bin 5 as well the product is already bound by the integer
+// pipe (first 4 / 5 / 6 bins: 907 / 904 / 920 ms per od solve at n = 1024).
 template <int P, int D>
 MD_INLINE void two_sum_pd(double a, double b, double& s, double& e) {
-    if constexpr (P <= 4 || D < 4) two_sum_int(a, b, s, e);
+    if constexpr (P <= 4 || D < 5) two_sum_int(a, b, s, e);
     else two_sum_fast(a, b, s, e);
 }
 

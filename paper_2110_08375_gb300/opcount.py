@@ -84,9 +84,9 @@ def _add(a, b, k=1):
 
 def two_sum_cost(p: int, d: int):
     """The two_sum form bin d of a p-limb operation uses (csrc/md.cuh,
-    two_sum_pd): the integer error for p <= 4 and for the first four bins of
+    two_sum_pd): the integer error for p <= 4 and for the first five bins of
     od; renormalisation counts as bin p."""
-    return TWO_SUM_INT if (p <= 4 or d < 4) else TWO_SUM_FAST
+    return TWO_SUM_INT if (p <= 4 or d < 5) else TWO_SUM_FAST
 
 
 def renorm_cost(p: int):
