@@ -58,6 +58,7 @@ struct SplitBuf {
     double* ptr;
     int64_t cap;
     const TcBuf* tc = nullptr;
+    bool whole_gpu = false;  // the launch has the GPU to itself: split K for whole waves
 };
 
 template <int P>
@@ -194,9 +195,29 @@ int tri_levels(int stage, cudaStream_t st, double* X, int64_t ldx, int64_t psx, 
     return MDLS_OK;
 }
 
-// Launches one md GEMM.  When the output grid alone would leave SMs idle,
-// the K range is split over grid.z (at most 16 ways, partials in `sb`) and a
-// reduction kernel adds the partials in a fixed order.
+// Resident blocks per SM of one md GEMM instance (occupancy query, once).
+template <int P, class AV, class BV>
+int gemm_blocks_per_sm() {
+    static const int nb = [] {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_kernel<P, AV, BV>, kGemmTile * gemm_tn<P>(), 0) !=
+                cudaSuccess ||
+            v < 1)
+            v = 1;
+        return v;
+    }();
+    return nb;
+}
+
+// Launches one md GEMM.  The K range may be split over grid.z (at most 16
+// ways, partials in `sb`, a reduction kernel adding them in a fixed order).
+// When the launch has the GPU to itself the split is the one that minimises
+// waves x K-chunk length, the launch's time when every block takes the same
+// time, so that small output grids fill the GPU and large ones do not end on
+// a mostly idle partial wave (an od product of 648 blocks on 456 block slots
+// is 1.4 waves, busy 71 % of the time; split in two over K, 2.8 of 3).  A
+// split must save 3 %.  Beside other launches small grids are split to about
+// twice the SM count.
 template <int P, class AV, class BV>
 int launch_gemm(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t N, int64_t K, AV a, BV b,
                 Dense c, bool neg, bool acc, bool upper_only = false) {
@@ -215,11 +236,32 @@ int launch_gemm(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t N, i
     const int64_t tiles = upper_only ? (gx * gy + gx) / 2 : gx * gy;
     const int64_t target = 2 * (int64_t)sm_count();
     int64_t S = 1;
-    if (tiles < target && K >= 4 * kGemmTile && sb.ptr != nullptr) {
-        S = (target + tiles - 1) / tiles;
-        if (S > 16) S = 16;
-        if (S > K / (2 * kGemmTile)) S = K / (2 * kGemmTile);
-        while (S > 1 && S * M * N > sb.cap) --S;
+    if (!sb.whole_gpu) {
+        // beside other launches (batched problems): fill twice the SM count
+        if (tiles < target && K >= 4 * kGemmTile && sb.ptr != nullptr) {
+            S = (target + tiles - 1) / tiles;
+            if (S > 16) S = 16;
+            if (S > K / (2 * kGemmTile)) S = K / (2 * kGemmTile);
+            while (S > 1 && S * M * N > sb.cap) --S;
+        }
+    } else if (K >= 4 * kGemmTile && sb.ptr != nullptr) {
+        const int64_t slots = (int64_t)sm_count() * gemm_blocks_per_sm<P, AV, BV>();
+        auto cost = [&](int64_t s, int64_t& parts) {
+            int64_t kc = (K + s - 1) / s;
+            kc = (kc + kGemmTile - 1) / kGemmTile * kGemmTile;
+            parts = (K + kc - 1) / kc;
+            return (tiles * parts + slots - 1) / slots * kc;
+        };
+        int64_t parts = 1;
+        int64_t best = cost(1, parts);
+        for (int64_t s = 2; s <= 16 && K / s >= 2 * kGemmTile; ++s) {
+            const int64_t c = cost(s, parts);
+            if (parts * M * N > sb.cap) break;
+            if (c * 100 < best * 97) {
+                best = c;
+                S = parts;
+            }
+        }
     }
     int64_t kchunk = K;
     if (S > 1) {
@@ -308,7 +350,7 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
                     L.tc_as_cap, L.tc_bs_cap, L.tc_sc_cap};
     }
     const SplitBuf sb{reinterpret_cast<double*>(ws + L.split), L.split_cap,
-                      L.tc_as_cap > 0 ? &tcb : nullptr};
+                      L.tc_as_cap > 0 ? &tcb : nullptr, !single_block};
     const int64_t tt2 = (int64_t)t * t;
     const int64_t psx = (int64_t)t * L.xcols;
     const int64_t ldw = m;
