@@ -1,7 +1,7 @@
 // Multiprecision arithmetic on the integer pipe: 24-bit digits with exact
 // int64 accumulation.
 //
-// On this GPU an FP64 warp instruction occupies its SM sub-partition for 64
+// On GB300 an FP64 warp instruction occupies its SM sub-partition for 64
 // cycles whatever the number of active lanes, while a 32-bit integer
 // multiply-add issues every 2 cycles with a 4.5-cycle dependent latency.  The
 // Householder panel (Section 3.1, step 1 of Algorithm 2) is a long chain of

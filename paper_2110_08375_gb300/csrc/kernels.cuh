@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kGemmTile* gemm_tn<P>())
 // gemv_kpar_kernel (A contiguous along i): lanes own 32 consecutive rows
 // (coalesced loads), the NW warps of a block take interleaved k and their
 // partial sums meet in a fixed tree in shared memory; grid.y splits the K
-// range further as in gemm_kernel.  On this GPU an FP64 warp instruction
+// range further as in gemm_kernel.  On GB300 an FP64 warp instruction
 // holds its SM sub-partition for 64 cycles whatever the number of active
 // lanes, so short products must be spread over many warps rather than run as
 // long per-thread chains.  gemv_warps_kernel (A contiguous along k): one warp

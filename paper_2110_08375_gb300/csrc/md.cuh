@@ -117,7 +117,7 @@ MD_INLINE double sum_error(double a, double b, double s) {
 // TwoSum: s = fl(a+b), e = (a+b) - s exactly, in two forms with the same
 // bits (s and e are unique).  two_sum_int: s is one FP64 addition and e comes
 // from sum_error on the integer pipe, which has some 30 times the FP64 pipe's
-// throughput on this GPU.  two_sum_fast: Dekker's Fast2Sum (3 FP64
+// throughput on GB300.  two_sum_fast: Dekker's Fast2Sum (3 FP64
 // operations) after ordering the operands by exponent with an integer compare
 // of the sign-cleared high words; fewer registers.  Knuth's branch-free
 // TwoSum would take 6 FP64 operations.
