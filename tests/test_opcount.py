@@ -72,3 +72,18 @@ def test_gemm_loop_cost_defers_renormalisation():
         full, rn = opcount.fma_cost(p)[0], opcount.renorm_cost(p)[0]
         assert opcount.gemm_fma_cost(p) == full - rn + rn / 16
         assert opcount.gemm_fma_cost(p, renorm_every=1) == full
+
+
+def test_two_sum_form_per_bin():
+    """The device's two_sum form by bin (csrc/md.cuh two_sum_pd): one FP64
+    addition (error on the integer pipe) for dd, qd and od's first five
+    bins; Fast2Sum (three) in od's last bins and renormalisation."""
+    for p in (2, 4):
+        assert all(opcount.two_sum_cost(p, d) == opcount.TWO_SUM_INT for d in range(p + 1))
+    assert [opcount.two_sum_cost(8, d)[0] for d in range(9)] == [1, 1, 1, 1, 1, 3, 3, 3, 3]
+    # od md FMA in the product loops: bins 0..4 hold 1+4+9+16+25 two_sums at
+    # one instruction, bins 5 and 6 36+49 at three; 28 two_prods; the last
+    # bin's 8 FMAs + 7 low parts + 49 errors; 13 renormalisation two_sums
+    # once per 16 steps
+    expect = (55 * 1 + 85 * 3) + 28 * 2 + (8 + 7 + 49) + 13 * 3 / 16
+    assert abs(opcount.gemm_fma_cost(8) - expect) < 1e-9
