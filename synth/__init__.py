@@ -189,3 +189,158 @@ def batched_shapes(count: int = 512, seed: int = 0, nmin: int = 32, nmax: int = 
 
 def batched_problem(idx: int, m: int, n: int, p: int, seed: int = 0):
     return lstsq_problem(p, m, n, seed, tag=f"batch{idx}")
+
+
+# ----------------------------------------------------------------------------
+# Precision-mode workload: A = U diag(sigma) V^T with exactly orthogonal U, V
+# and singular values log-spaced over a chosen condition number.
+#
+# With Sylvester's Hadamard matrix H_N (entries (-1)^popcount(i & j)):
+#   U = D_u H_m[:, c] / sqrt(m)   (n columns of the randomised H_m: D_u random
+#                                  signs, c a seeded random subset of columns),
+#   V^T = H_n[pi, :] D_v / sqrt(n) (pi a seeded permutation, D_v random signs),
+#   sigma_k = d_k / sqrt(2), d_k = D_k 2^-20, D_k = round(2^20 kappa^(k/(n-1))).
+# U and V are exactly orthogonal.  For m = 4^a and n = 2 * 4^b the scale
+# sqrt(2) / (sqrt(m) sqrt(n)) is a power of two, so every entry of
+#   A = 2^-shift_a D_u H_m[:, c] diag(D) H_n[pi, :] D_v
+# is an exact dyadic number (an integer below 2^51 times 2^-shift_a), and
+# kappa = max sigma / min sigma.  Only integer transforms are used (Walsh-
+# Hadamard butterflies on int64 and on Python integers); every value is exact
+# and the md values handed out are those exact numbers split into doubles by
+# bit slicing (no rounding).
+# ----------------------------------------------------------------------------
+
+def _fwht_int64(Z: np.ndarray) -> np.ndarray:
+    """H_N Z for Sylvester's H_N (N = Z.shape[0], a power of two), exact in
+    int64 while the magnitudes stay below 2^63."""
+    Z = Z.copy()
+    N = Z.shape[0]
+    h = 1
+    while h < N:
+        Z = Z.reshape(N // (2 * h), 2, h, *Z.shape[1:])
+        a = Z[:, 0].copy()
+        b = Z[:, 1]
+        Z[:, 0] = a + b
+        Z[:, 1] = a - b
+        Z = Z.reshape(N, *Z.shape[3:])
+        h *= 2
+    return Z
+
+
+def fwht_py(v: list) -> list:
+    """H_N v for a list of Python integers (exact)."""
+    v = list(v)
+    N = len(v)
+    h = 1
+    while h < N:
+        for s in range(0, N, 2 * h):
+            for i in range(s, s + h):
+                a, b = v[i], v[i + h]
+                v[i], v[i + h] = a + b, a - b
+        h *= 2
+    return v
+
+
+def split_exact(num: int, shift: int, p: int) -> list:
+    """num * 2^-shift (a Python integer numerator) as p doubles by bit
+    slicing: limb 0 holds the leading 53 bits, limb 1 the next 53, and so on
+    (each limb below one ulp of the one above; exact when the value has at
+    most 53 p significant bits, otherwise the bits beyond are dropped)."""
+    import math
+    out = [0.0] * p
+    if num == 0:
+        return out
+    sgn = -1 if num < 0 else 1
+    a = -num if num < 0 else num
+    top = a.bit_length()
+    for i in range(p):
+        lo = top - 53 * (i + 1)
+        if lo > 0:
+            chunk = (a >> lo) & ((1 << 53) - 1)
+            out[i] = sgn * math.ldexp(float(chunk), lo - shift)
+        else:
+            chunk = a & ((1 << (53 + lo)) - 1) if 53 + lo > 0 else 0
+            out[i] = sgn * math.ldexp(float(chunk), -shift)
+            break
+    return out
+
+
+def modes_structure(m: int = 4096, n: int = 2048, kappa: float = 1e6, seed: int = 0,
+                    tag: str = "modes") -> dict:
+    """The random choices of the precision-mode matrix (see above): signs
+    du (m), dv (n), the column subset c (n of range(m)), the permutation pi
+    (n) and the integer singular-value numerators D (n), with the scale
+    exponents (A = 2^-shift_a D_u H_m[:, c] diag(D) H_n[pi, :] D_v)."""
+    lm, ln = int(math.log2(m)), int(math.log2(n))
+    if 2 ** lm != m or 2 ** ln != n or lm % 2 != 0 or ln % 2 != 1 or n > m:
+        raise ValueError("needs m = 4^a >= n = 2 * 4^b")
+    lab = f"{tag}/{m}x{n}/k{kappa:g}/s{seed}"
+    du = np.where(unit(seed, lab + "/du", m) < 0.5, -1, 1).astype(np.int64)
+    dv = np.where(unit(seed, lab + "/dv", n) < 0.5, -1, 1).astype(np.int64)
+    c = np.sort(np.argsort(unit(seed, lab + "/c", m), kind="stable")[:n]).astype(np.int64)
+    pi = np.argsort(unit(seed, lab + "/pi", n), kind="stable").astype(np.int64)
+    k = np.arange(n, dtype=np.float64)
+    D = np.rint(np.power(float(kappa), k / (n - 1)) * 2.0 ** 20).astype(np.int64)
+    # 1/sqrt(m) = 2^-(lm/2) and 1/(sqrt(2) sqrt(n)) = 2^-((ln+1)/2); d = D 2^-20
+    shift_a = lm // 2 + (ln + 1) // 2 + 20
+    return {"m": m, "n": n, "kappa": kappa, "du": du, "dv": dv, "c": c, "pi": pi, "D": D,
+            "shift_a": shift_a, "shift_sigma": 20}
+
+
+def hadamard_rows(rows: np.ndarray, N: int) -> np.ndarray:
+    """Rows `rows` of Sylvester's H_N as int64 (+-1): (-1)^popcount(r & j)."""
+    j = np.arange(N, dtype=np.int64)
+    par = (np.bitwise_count(rows[:, None] & j[None, :]) & 1).astype(np.int64)
+    return 1 - 2 * par
+
+
+def modes_matrix_int(st: dict) -> np.ndarray:
+    """Integer numerators Aint (m x n, row-major [i][j]) with A = Aint 2^-shift_a."""
+    m, n = st["m"], st["n"]
+    M = hadamard_rows(st["pi"], n) * st["D"][:, None] * st["dv"][None, :]   # diag(D) H_n[pi, :] D_v
+    Z = np.zeros((m, n), dtype=np.int64)
+    Z[st["c"]] = M
+    Y = _fwht_int64(Z)                                                      # H_m[:, c] diag(D) ...
+    return Y * st["du"][:, None]
+
+
+def modes_apply_int(st: dict, xnum: list) -> list:
+    """A x for x = xnum 2^-e (Python integers), as numerators over 2^-(shift_a+e)."""
+    m, n = st["m"], st["n"]
+    v = [int(st["dv"][j]) * xnum[j] for j in range(n)]
+    v = fwht_py(v)
+    z = [0] * m
+    for k in range(n):
+        z[int(st["c"][k])] = int(st["D"][k]) * v[int(st["pi"][k])]
+    z = fwht_py(z)
+    return [int(st["du"][i]) * z[i] for i in range(m)]
+
+
+def modes_problem(p: int, m: int = 4096, n: int = 2048, kappa: float = 1e6, seed: int = 0,
+                  consistent: bool = True, tag: str = "modes") -> dict:
+    """The precision-mode least-squares problem in p limbs.
+
+    A (p, n, m): exact doubles in limb 0 (|A_ij| 2^shift_a < 2^51), zeros
+    below.  consistent=True: x* ~ U[-1,1) doubles and b = A x* exactly (at
+    most about 130 significant bits, so exact in quad and octo double), so x*
+    is the exact least-squares solution.  consistent=False: b ~ U[-1,1) in p
+    limbs (the recipe of md_vector); the solution then has the closed form
+    V diag(1/sigma) U^T b, which the oracle evaluates from the structure.
+    Returns a dict with A, b, xstar (or None) and the structure."""
+    st = modes_structure(m, n, kappa, seed, tag)
+    Aint = modes_matrix_int(st)
+    A = np.zeros((p, n, m), dtype=np.float64)
+    A[0] = (Aint.T).astype(np.float64) * 2.0 ** (-st["shift_a"])
+    lab = f"{tag}/{m}x{n}/k{kappa:g}/s{seed}/p{p}"
+    xstar = None
+    if consistent:
+        x0 = sym(seed, lab + "/x", n)
+        xnum = [int(np.ldexp(v, 53)) for v in x0]          # x = xnum 2^-53 exactly
+        bnum = modes_apply_int(st, xnum)
+        sh = st["shift_a"] + 53
+        b = np.array([split_exact(v, sh, p) for v in bnum]).T.copy()
+        xstar = np.zeros((p, n))
+        xstar[0] = x0
+    else:
+        b = md_vector(p, m, seed, lab + "/b")
+    return {"A": np.ascontiguousarray(A), "b": np.ascontiguousarray(b), "xstar": xstar, "structure": st}
