@@ -239,6 +239,27 @@ int mdls_batched_modes(void* plan, int* modes);
 void mdls_batched_destroy(void* plan);
 
 /*
+ * mdls_wait_check -- diagnostic of the bounded device waits (failure
+ * detection).  The Householder panel runs its column blocks side by side,
+ * each waiting on flags that the blocks before it publish (Section 3: the
+ * columns of a tile are reduced one after the other); every such wait gives
+ * up after a limit, records MDLS_ERR_TIMEOUT in the workspace status and
+ * lets the kernel return, so that a lost block cannot hang the GPU.  This
+ * call runs that same wait in a two-block kernel: block 1 waits for a flag
+ * that block 0 publishes when publish = 1 and never publishes when
+ * publish = 0.
+ *   ws: device workspace of at least MDLS_WAIT_CHECK_WORKSPACE bytes,
+ *   256-byte aligned (its header and the flag are cleared by the call).
+ *   limit_ns: the wait's limit, 1e3 .. 1e10 ns (the library's own calls use
+ *   2 s).
+ * Afterwards mdls_read_status(ws) gives MDLS_ERR_TIMEOUT (publish = 0, after
+ * about limit_ns) or MDLS_OK (publish = 1).  Returns MDLS_OK,
+ * MDLS_ERR_WORKSPACE, MDLS_ERR_ARG or MDLS_ERR_CUDA.
+ */
+#define MDLS_WAIT_CHECK_WORKSPACE 512
+int mdls_wait_check(void* ws, size_t ws_bytes, uint64_t limit_ns, int publish, void* stream);
+
+/*
  * mdls_read_status -- waits for `stream`, then copies the device status word
  * of the workspace `ws` (MDLS_OK, MDLS_ERR_SINGULAR or MDLS_ERR_TIMEOUT) to
  * *status.  Returns MDLS_OK or MDLS_ERR_CUDA.

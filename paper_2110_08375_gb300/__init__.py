@@ -87,6 +87,7 @@ def lib() -> C.CDLL:
     L.mdls_batched_destroy.argtypes = [vp]
     L.mdls_batched_destroy.restype = None
     L.mdls_vec_op.argtypes = [C.c_int, C.c_int, i64, vp, i64, vp, i64, vp, i64, vp]
+    L.mdls_wait_check.argtypes = [vp, sz, C.c_uint64, C.c_int, vp]
     _lib = L
     return L
 
@@ -220,6 +221,22 @@ def mdls_vec_op(op: str, a, b=None, c=None, stream=None):
     if rc != MDLS_OK:
         raise MdlsError(rc, "mdls_vec_op")
     return c
+
+
+WAIT_CHECK_WORKSPACE = 512
+
+
+def mdls_wait_check(limit_ns: int, publish: bool, ws=None, stream=None):
+    """Runs the library's bounded device wait with the given limit on a flag
+    that is published (publish=True) or never published; returns the
+    workspace, whose status then reads MDLS_OK or MDLS_ERR_TIMEOUT."""
+    if ws is None:
+        ws = workspace(WAIT_CHECK_WORKSPACE)
+    rc = lib().mdls_wait_check(ws.data_ptr(), ws.numel() * ws.element_size(), int(limit_ns),
+                               int(bool(publish)), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_wait_check")
+    return ws
 
 
 N_STAGES = 9

@@ -1,0 +1,312 @@
+// Step 2 of Algorithm 1 (Section 2) in one persistent launch: the tile loop
+// i = N..1 of x_i := U_i^{-1} y_i and y_j := y_j - A_{j,i} x_i, with the
+// inverted diagonal tiles U_i^{-1} already in place (step 1).
+//
+// The paper launches one kernel per tile step.  On GB300 the FP64 pipe
+// retires one warp instruction per 64 cycles per SM sub-partition, so a warp
+// that updates 32 rows with a whole tile of 128 columns (128 md FMAs per
+// lane) needs 167 us in quad double however the launch is arranged, and a
+// launch per step waits for its slowest warp.  Here the steps overlap:
+//
+//  * bulk work -- y_c := y_c - A_{c,i} x_i for every 32-row chunk c that lies
+//    at least two tiles above tile i -- is a queue of (chunk, tile) tasks,
+//    one warp each, taken in order of i; a task computes its product as soon
+//    as x_i is published and applies it to y_c when the chunk's earlier
+//    updates (tiles N..i+1) are in, so every y_c receives its terms in the
+//    same order in every run (deterministic);
+//  * critical work -- the step from x_i to x_{i-1}: the update of tile i-1's
+//    rows by x_i and the product x_{i-1} = U_{i-1}^{-1} y_{i-1} -- runs on a
+//    few reserved SMs (one warp per SM sub-partition, so each has its FP64
+//    pipe to itself), with the k range of both products split into slices of
+//    kBsSlice columns over many warps; the last warp to finish a chunk adds
+//    the slices' partial sums in slice order.
+//
+// Every wait is bounded (wait_ge): a wait that runs out records
+// MDLS_ERR_TIMEOUT and every warp leaves at its next wait or task.
+// Data written by other SMs is read with ld.global.cg (L2), never from L1.
+#pragma once
+#include "kernels.cuh"
+
+namespace mdls {
+
+constexpr int kBsSlice = 8;       // columns per slice of the critical products
+constexpr int kBsCritSms = 16;    // SMs reserved for the critical path
+constexpr int kBsMaxSm = 1024;    // slots of the per-SM role claim
+
+// Counters of the persistent back substitution (unsigned ints, zeroed by the
+// host before the launch).
+struct BsCtr {
+    int64_t bulk_head, crit_head, crit_claims, sm_claim, sm_slot, bulk_done, cu_cnt, xt_cnt, yfin, xready, total;
+    __host__ __device__ static BsCtr make(int64_t nchunks, int64_t N) {
+        BsCtr c;
+        c.bulk_head = 0;
+        c.crit_head = 32;   // separate 128-byte lines for the queue heads
+        c.crit_claims = 64;
+        c.sm_claim = 96;
+        c.sm_slot = c.sm_claim + kBsMaxSm;
+        c.bulk_done = c.sm_slot + kBsMaxSm;
+        c.cu_cnt = c.bulk_done + nchunks;
+        c.xt_cnt = c.cu_cnt + nchunks;
+        c.yfin = c.xt_cnt + nchunks;
+        c.xready = c.yfin + N;
+        c.total = c.xready + N;
+        return c;
+    }
+};
+
+struct BsPersistArgs {
+    const double* R;
+    int64_t ldr, psr;
+    const double* D;     // inverted diagonal tiles: tile i at D + i t^2, column-major, ld t
+    int64_t dps;         // plane stride of D
+    double* yb;          // working right-hand side, P planes of n
+    double* x;
+    int64_t psx;
+    double* cu_part;     // [limb][chunk][slice][lane] partial sums of the critical updates
+    double* xt_part;     // [limb][chunk][slice][lane] partial sums of x = U^{-1} y
+    int64_t part_ps;     // plane stride of the partial-sum buffers
+    unsigned int* ctr;
+    int64_t n;
+    int t, N, nchunks, S, KS, ncrit;
+    WsHeader* hdr;
+};
+
+// Lane 0 waits until *c >= want (bounded); the result is broadcast to the warp.
+DEV_INLINE bool warp_wait_ge(const unsigned int* c, unsigned int want, WsHeader* h) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        const volatile unsigned int* vc = c;
+        const volatile int* verr = &h->bar_error;
+        if (*vc < want) {
+            const unsigned long long lim0 = *reinterpret_cast<const volatile unsigned long long*>(&h->wait_ns);
+            const unsigned long long lim = lim0 ? lim0 : kWaitDefaultNs;
+            const unsigned long long t0 = globaltimer_ns();
+            while (*vc < want) {
+                if (*verr) {
+                    ok = 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > lim) {
+                    atomicExch(&h->bar_error, 1);
+                    set_status(&h->status, MDLS_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
+template <int P>
+DEV_INLINE md<P> ld_md_cg(const double* ptr, int64_t ps, int64_t off) {
+    md<P> r;
+#pragma unroll
+    for (int l = 0; l < P; ++l) r.v[l] = __ldcg(ptr + l * ps + off);
+    return r;
+}
+
+// Publishes the warp's stores, then adds 1 to *c (lane 0); returns the old
+// value to every lane.
+DEV_INLINE unsigned int warp_publish(unsigned int* c) {
+    __threadfence();
+    __syncwarp();
+    unsigned int old = 0;
+    if ((threadIdx.x & 31) == 0) old = atomicAdd(c, 1u);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    __threadfence();
+    return old;
+}
+
+DEV_INLINE int tile_width(int64_t n, int t, int64_t j) {
+    const int64_t w = n - j * t;
+    return (int)(w < t ? w : t);
+}
+
+// sum_{k in [k0, k1)} A(r, k) x_k with lanes on rows (A column-major, coalesced)
+template <int P>
+DEV_INLINE md<P> rows_times_x(const double* A, int64_t lda, int64_t psa, int64_t r, bool rv, int64_t k0,
+                              int64_t k1, const double* x, int64_t psx) {
+    double bins[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) bins[l] = 0.0;
+    int cnt = 0;
+    for (int64_t k = k0; k < k1; ++k) {
+        md<P> a, xv;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            a.v[l] = rv ? A[l * psa + k * lda + r] : 0.0;
+            xv.v[l] = __ldcg(x + l * psx + k);
+        }
+        md_fma_bins<P>(bins, a, xv);
+        if ((++cnt & 15) == 0) md_bins_renorm<P>(bins);
+    }
+    return md_from_bins<P>(bins);
+}
+
+// Number of slices of tile j's columns that meet rows [32 cl, 32 cl + 32) of
+// the upper triangular U_j^{-1} (slices wholly left of the chunk's diagonal
+// are zero) and lie inside the tile.
+DEV_INLINE int xt_needed(int cl, int tt, int S) {
+    int cnt = 0;
+    for (int s = 0; s < S; ++s)
+        if (s * kBsSlice < tt && s * kBsSlice + kBsSlice - 1 >= 32 * cl) ++cnt;
+    return cnt;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
+    __shared__ int role;  // 0 bulk, 1 critical, 2 idle
+    const int lane = threadIdx.x & 31;
+    unsigned int* ctr = a.ctr;
+    const BsCtr C = BsCtr::make(a.nchunks, a.N);
+    if (threadIdx.x == 0) {
+        // the first block on each SM asks for a critical slot; the first
+        // ncrit to ask get one, and the other blocks on their SMs stay idle
+        // so that the critical warps have the SM's FP64 pipes to themselves
+        unsigned int smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        unsigned int* sm_role = ctr + C.sm_claim + (smid % kBsMaxSm);   // 0 unset, 1 bulk SM, 2 critical SM
+        unsigned int* sm_slot = ctr + C.sm_slot + (smid % kBsMaxSm);
+        const unsigned int slot = atomicAdd(sm_slot, 1u);
+        if (slot == 0) {
+            const unsigned int g = atomicAdd(ctr + C.crit_claims, 1u);
+            role = g < (unsigned)a.ncrit ? 1 : 0;
+            __threadfence();
+            atomicExch(sm_role, role == 1 ? 2u : 1u);
+        } else {
+            const volatile unsigned int* vr = sm_role;
+            const unsigned long long t0 = globaltimer_ns();
+            int r = -1;
+            while (r < 0) {
+                const unsigned int v = *vr;
+                if (v != 0) r = v == 2 ? 2 : 0;
+                else if (globaltimer_ns() - t0 > kWaitDefaultNs) {
+                    atomicExch(&a.hdr->bar_error, 1);
+                    set_status(&a.hdr->status, MDLS_ERR_TIMEOUT);
+                    r = 2;
+                }
+            }
+            role = r;
+        }
+    }
+    __syncthreads();
+    if (role == 2) return;
+    const int64_t n = a.n;
+    const int t = a.t, N = a.N, S = a.S, tc = t / 32;
+    const int64_t pps = a.part_ps;
+
+    if (role == 1) {
+        // critical queue: phase 0 = x_{N-1}; then for i = N-1 .. 1, phase
+        // 2(N-1-i)+1 = update of tile i-1's rows by x_i, phase 2(N-1-i)+2 =
+        // x_{i-1}; KS task slots per phase (unused slots are skipped)
+        const int64_t total = (int64_t)(2 * N - 1) * a.KS;
+        for (;;) {
+            if (*reinterpret_cast<volatile int*>(&a.hdr->bar_error)) return;
+            unsigned int q = 0;
+            if (lane == 0) q = atomicAdd(ctr + C.crit_head, 1u);
+            q = __shfl_sync(0xffffffffu, q, 0);
+            if ((int64_t)q >= total) return;
+            const int phase = (int)(q / a.KS), k = (int)(q % a.KS);
+            if (phase % 2 == 1) {
+                // update of tile j = i - 1 (full width) by x_i, slice s of tile i
+                const int i = N - 1 - (phase - 1) / 2, j = i - 1;
+                const int cl = k / S, s = k % S;
+                if (cl >= tc) continue;
+                const int64_t c = (int64_t)j * tc + cl;
+                if (!warp_wait_ge(ctr + C.xready + i, (unsigned)((tile_width(n, t, i) + 31) / 32), a.hdr)) return;
+                const int64_t r = c * 32 + lane;
+                int64_t k0 = (int64_t)i * t + (int64_t)s * kBsSlice;
+                int64_t k1 = k0 + kBsSlice;
+                const int64_t kend = (int64_t)i * t + tile_width(n, t, i);
+                if (k1 > kend) k1 = kend;
+                if (k0 > k1) k0 = k1;
+                const md<P> part = rows_times_x<P>(a.R, a.ldr, a.psr, r, true, k0, k1, a.x, a.psx);
+                st_md<P>(a.cu_part, pps, (c * S + s) * 32 + lane, part);
+                const unsigned old = warp_publish(ctr + C.cu_cnt + c);
+                if (old != (unsigned)(S - 1)) continue;
+                // last slice of chunk c: wait for its bulk updates (tiles N-1 .. i+1),
+                // then y_c -= slices 0 .. S-1 in order
+                if (!warp_wait_ge(ctr + C.bulk_done + c, (unsigned)(N - 1 - i), a.hdr)) return;
+                md<P> y = ld_md_cg<P>(a.yb, n, r);
+                for (int s2 = 0; s2 < S; ++s2) y = md_sub<P>(y, ld_md_cg<P>(a.cu_part, pps, (c * S + s2) * 32 + lane));
+                st_md<P>(a.yb, n, r, y);
+                warp_publish(ctr + C.yfin + j);
+            } else {
+                // x_j = U_j^{-1} y_j: output chunk cl of tile j, slice s of its columns
+                const int j = N - 1 - phase / 2;
+                const int tt = tile_width(n, t, j);
+                const int cl = k / S, s = k % S;
+                if (cl * 32 >= tt) continue;
+                if (!(s * kBsSlice < tt && s * kBsSlice + kBsSlice - 1 >= 32 * cl)) continue;
+                if (j < N - 1 && !warp_wait_ge(ctr + C.yfin + j, (unsigned)tc, a.hdr)) return;
+                const int rl = cl * 32 + lane;  // row within the tile
+                const bool rv = rl < tt;
+                const double* Dj = a.D + (int64_t)j * t * t;
+                const double* yj = a.yb + (int64_t)j * t;
+                double bins[P];
+#pragma unroll
+                for (int l = 0; l < P; ++l) bins[l] = 0.0;
+                const int k0 = s * kBsSlice, k1 = (k0 + kBsSlice) < tt ? (k0 + kBsSlice) : tt;
+                for (int kk = k0; kk < k1; ++kk) {
+                    md<P> dv, yv;
+                    const bool in = rv && kk >= rl;  // U^{-1} is upper triangular
+#pragma unroll
+                    for (int l = 0; l < P; ++l) {
+                        dv.v[l] = in ? Dj[l * a.dps + (int64_t)kk * t + rl] : 0.0;
+                        yv.v[l] = __ldcg(yj + l * n + kk);
+                    }
+                    md_fma_bins<P>(bins, dv, yv);
+                }
+                const int64_t c = (int64_t)j * tc + cl;
+                st_md<P>(a.xt_part, pps, (c * S + s) * 32 + lane, md_from_bins<P>(bins));
+                const unsigned old = warp_publish(ctr + C.xt_cnt + c);
+                if (old != (unsigned)(xt_needed(cl, tt, S) - 1)) continue;
+                // last slice: x = the slices' sum in slice order
+                md<P> xs = md_zero<P>();
+                bool first = true;
+                for (int s2 = 0; s2 < S; ++s2) {
+                    if (!(s2 * kBsSlice < tt && s2 * kBsSlice + kBsSlice - 1 >= 32 * cl)) continue;
+                    const md<P> v = ld_md_cg<P>(a.xt_part, pps, (c * S + s2) * 32 + lane);
+                    xs = first ? v : md_add<P>(xs, v);
+                    first = false;
+                }
+                if (rv) st_md<P>(a.x, a.psx, (int64_t)j * t + rl, xs);
+                warp_publish(ctr + C.xready + j);
+            }
+        }
+    }
+
+    // bulk queue: tasks (c, i) for i = N-1 .. 2 and chunks c < (i-1) tc in
+    // decreasing order; step a = N-1-i holds (i-1) tc tasks
+    int sa = 0;
+    int64_t base = 0;  // first task of step sa
+    for (;;) {
+        if (*reinterpret_cast<volatile int*>(&a.hdr->bar_error)) return;
+        unsigned int q = 0;
+        if (lane == 0) q = atomicAdd(ctr + C.bulk_head, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        while (sa < N - 2 && (int64_t)q >= base + (int64_t)(N - 2 - sa) * tc) {
+            base += (int64_t)(N - 2 - sa) * tc;
+            ++sa;
+        }
+        if (sa >= N - 2) return;
+        const int i = N - 1 - sa;
+        const int64_t c = (int64_t)(i - 1) * tc - 1 - ((int64_t)q - base);
+        if (!warp_wait_ge(ctr + C.xready + i, (unsigned)((tile_width(n, t, i) + 31) / 32), a.hdr)) return;
+        const int64_t r = c * 32 + lane;
+        const int64_t k0 = (int64_t)i * t, k1 = k0 + tile_width(n, t, i);
+        const md<P> acc = rows_times_x<P>(a.R, a.ldr, a.psr, r, true, k0, k1, a.x, a.psx);
+        // apply in the chunk's fixed order: tiles N-1, N-2, ..., i+1 before i
+        if (!warp_wait_ge(ctr + C.bulk_done + c, (unsigned)(N - 1 - i), a.hdr)) return;
+        const md<P> y = md_sub<P>(ld_md_cg<P>(a.yb, n, r), acc);
+        st_md<P>(a.yb, n, r, y);
+        warp_publish(ctr + C.bulk_done + c);
+    }
+}
+
+}  // namespace mdls

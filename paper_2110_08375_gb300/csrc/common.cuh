@@ -101,12 +101,11 @@ struct ViewUpperT {
 // live at the start of every workspace the caller hands in.
 // ----------------------------------------------------------------------------
 struct WsHeader {
-    int status;            // first error seen on the device (0 = none)
+    int status;                  // first error seen on the device (0 = none)
     int pad0;
-    unsigned int reserved0;
-    unsigned int reserved1;
-    int bar_error;           // set by a bounded wait that gave up: later waits fail fast
-    int pad2[59];            // header is 256 bytes
+    unsigned long long wait_ns;  // limit of every bounded wait, ns (0 = the 2 s default)
+    int bar_error;               // set by a bounded wait that gave up: later waits fail fast
+    int pad2[59];                // header is 256 bytes
 };
 static_assert(sizeof(WsHeader) == 256, "workspace header must be 256 bytes");
 

@@ -58,18 +58,30 @@ DEV_INLINE md<P> md_select(bool c, const md<P>& a, const md<P>& b) {
     return r;
 }
 
-constexpr long long kFlagTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
+// Bounded waits measure wall time on the GPU's global timer (ns), so that
+// the limit does not move with the SM clock.  The limit is the workspace
+// header's wait_ns, or 2 s when that is 0 (every entry point clears the
+// header, so the default applies unless a caller sets it afterwards).
+constexpr unsigned long long kWaitDefaultNs = 2000000000ull;
 
-// Waits (thread 0 only) until *flag == want.  Bounded: on timeout it records
-// MDLS_ERR_TIMEOUT and returns false.  Also returns false when another block
-// has already failed.
+DEV_INLINE unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits (thread 0 only) until *flag == want.  Bounded: when the limit runs
+// out it records MDLS_ERR_TIMEOUT, raises the header's failure flag and
+// returns false.  Also returns false as soon as another block has failed.
 DEV_INLINE bool wait_flag(const unsigned int* flag, unsigned int want, WsHeader* h) {
     const volatile unsigned int* vf = flag;
     const volatile int* verr = &h->bar_error;
-    long long t0 = clock64();
+    const unsigned long long lim0 = *reinterpret_cast<const volatile unsigned long long*>(&h->wait_ns);
+    const unsigned long long lim = lim0 ? lim0 : kWaitDefaultNs;
+    const unsigned long long t0 = globaltimer_ns();
     while (*vf != want) {
         if (*verr) return false;
-        if (clock64() - t0 > kFlagTimeoutCycles) {
+        if (globaltimer_ns() - t0 > lim) {
             atomicExch(&h->bar_error, 1);
             set_status(&h->status, MDLS_ERR_TIMEOUT);
             return false;
@@ -78,6 +90,21 @@ DEV_INLINE bool wait_flag(const unsigned int* flag, unsigned int want, WsHeader*
     }
     __threadfence();
     return true;
+}
+
+// Diagnostic of the bounded wait (mdls_wait_check): block 1 waits, with the
+// limit in the header, for a flag that block 0 publishes only when
+// `publish` is set.  Launched cooperatively, so both blocks are resident.
+static __global__ void wait_check_kernel(unsigned int* flag, WsHeader* h, int publish) {
+    if (threadIdx.x != 0) return;
+    if (blockIdx.x == 0) {
+        if (publish) {
+            __threadfence();
+            atomicExch(flag, 1u);
+        }
+        return;
+    }
+    wait_flag(flag, 1u, h);
 }
 
 // ----------------------------------------------------------------------------

@@ -107,3 +107,15 @@ def test_library_has_no_oracle_dependency():
         if src.endswith((".cu", ".cuh", ".h", ".py")):
             text = open(src).read()
             assert "mdref" not in text and "import oracle" not in text, src
+
+
+def test_wait_check_argument_errors(L):
+    vp = C.c_void_p
+    fake = vp(1 << 20)
+    L.mdls_wait_check.argtypes = [vp, C.c_size_t, C.c_uint64, C.c_int, vp]
+    assert L.mdls_wait_check(None, 512, 10**6, 0, None) == -3
+    assert L.mdls_wait_check(fake, 256, 10**6, 0, None) == -3          # too small
+    assert L.mdls_wait_check(vp((1 << 20) + 64), 512, 10**6, 0, None) == -3   # misaligned
+    assert L.mdls_wait_check(fake, 512, 10, 0, None) == -1             # limit below 1 us
+    assert L.mdls_wait_check(fake, 512, 2 * 10**10, 0, None) == -1     # limit above 10 s
+    assert L.mdls_wait_check(fake, 512, 10**6, 2, None) == -1
