@@ -120,6 +120,29 @@ int mdls_backsub(int prec, int64_t n, const double* R, int64_t ldr, int64_t psr,
 size_t mdls_backsub_workspace(int prec, int64_t n, int tile);
 
 /*
+ * mdls_set_backsub_schedule -- how step 2 of Algorithm 1 (x_i := U_i^{-1} y_i,
+ * y_j := y_j - A_{j,i} x_i for i = N..1) is launched, for every later call
+ * of this process (mdls_backsub, mdls_backsub_noalloc and the back
+ * substitution inside mdls_lstsq):
+ *   MDLS_BS_PER_STEP: as in the paper, kernels per tile step, each step
+ *     spread over the whole GPU;
+ *   MDLS_BS_PERSISTENT: one cooperative launch in which the steps overlap:
+ *     the updates of rows two or more tiles above the current tile run from
+ *     a task queue on most SMs while a few reserved SMs carry the chain
+ *     x_i -> x_{i-1}; same arithmetic, each y_j receives its terms in the
+ *     same fixed order (results are deterministic, though not bitwise equal
+ *     to the per-step schedule's);
+ *   MDLS_BS_AUTO (default): persistent in double double from 8 tiles on and
+ *     in quad double from n = 8192 on, per step otherwise (measured choice).
+ * Tiles that are not a multiple of 32 wide always run per step.  Not meant
+ * to change while calls are in flight.  Returns MDLS_OK or MDLS_ERR_ARG.
+ */
+#define MDLS_BS_AUTO 0
+#define MDLS_BS_PER_STEP 1
+#define MDLS_BS_PERSISTENT 2
+int mdls_set_backsub_schedule(int schedule);
+
+/*
  * mdls_backsub_noalloc -- the same back substitution as mdls_backsub, for
  * callers that cannot allocate device memory when they call: a plugin inside
  * a host framework that owns all device memory through its own allocator, a
@@ -131,7 +154,7 @@ size_t mdls_backsub_workspace(int prec, int64_t n, int tile);
  *   MDLS_BACKSUB_NOALLOC_MAX_BYTES inside the library, held by every GPU that
  *   loads the library until the process exits.  Problems needing more
  *   scratch than that (mdls_backsub_workspace(prec, n, tile) bytes; at tile
- *   128 about n <= 8000 in dd, 3900 in qd, 1900 in od) are rejected with
+ *   128: n <= 6400 in dd, 3200 in qd, 1536 in od) are rejected with
  *   MDLS_ERR_WORKSPACE before anything is enqueued.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any

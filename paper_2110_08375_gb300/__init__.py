@@ -88,6 +88,7 @@ def lib() -> C.CDLL:
     L.mdls_batched_destroy.restype = None
     L.mdls_vec_op.argtypes = [C.c_int, C.c_int, i64, vp, i64, vp, i64, vp, i64, vp]
     L.mdls_wait_check.argtypes = [vp, sz, C.c_uint64, C.c_int, vp]
+    L.mdls_set_backsub_schedule.argtypes = [C.c_int]
     _lib = L
     return L
 
@@ -221,6 +222,17 @@ def mdls_vec_op(op: str, a, b=None, c=None, stream=None):
     if rc != MDLS_OK:
         raise MdlsError(rc, "mdls_vec_op")
     return c
+
+
+BS_AUTO, BS_PER_STEP, BS_PERSISTENT = 0, 1, 2
+
+
+def mdls_set_backsub_schedule(schedule: int) -> None:
+    """Step 2 of the back substitution per tile step (BS_PER_STEP), in one
+    persistent launch (BS_PERSISTENT) or chosen by size (BS_AUTO)."""
+    rc = lib().mdls_set_backsub_schedule(int(schedule))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_set_backsub_schedule")
 
 
 WAIT_CHECK_WORKSPACE = 512

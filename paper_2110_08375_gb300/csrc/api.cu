@@ -24,6 +24,11 @@ MDLS_DECLARE(8)
 
 using namespace mdls;
 
+int& mdls::bs_schedule_ref() {
+    static int s = MDLS_BS_AUTO;
+    return s;
+}
+
 static bool prec_ok(int p) { return p == 2 || p == 4 || p == 8; }
 
 static bool ws_ok(const void* ws, size_t have, size_t need) {
@@ -147,6 +152,13 @@ int mdls_vec_op(int prec, int op, int64_t count, const double* a, int64_t psa, c
         case 4: return vec_entry_p4(op, count, a, psa, b, psb, c, psc, st);
         default: return vec_entry_p8(op, count, a, psa, b, psb, c, psc, st);
     }
+}
+
+int mdls_set_backsub_schedule(int schedule) {
+    if (schedule != MDLS_BS_AUTO && schedule != MDLS_BS_PER_STEP && schedule != MDLS_BS_PERSISTENT)
+        return MDLS_ERR_ARG;
+    bs_schedule_ref() = schedule;
+    return MDLS_OK;
 }
 
 int mdls_read_status(const void* ws, int* status, void* stream) {

@@ -2,54 +2,63 @@
 // i = N..1 of x_i := U_i^{-1} y_i and y_j := y_j - A_{j,i} x_i, with the
 // inverted diagonal tiles U_i^{-1} already in place (step 1).
 //
-// The paper launches one kernel per tile step.  On GB300 the FP64 pipe
-// retires one warp instruction per 64 cycles per SM sub-partition, so a warp
-// that updates 32 rows with a whole tile of 128 columns (128 md FMAs per
-// lane) needs 167 us in quad double however the launch is arranged, and a
-// launch per step waits for its slowest warp.  Here the steps overlap:
+// The paper launches kernels per tile step.  On GB300 the FP64 pipe retires
+// one warp instruction per 64 cycles per SM sub-partition, so a warp that
+// updates 32 rows with a whole tile of 128 columns (128 md FMAs per lane)
+// needs 167 us in quad double however the launch is arranged; a launch per
+// step waits for its slowest warp, and a chain of such tasks between x_i and
+// x_{i-2} would set the pace of the whole solve.  Here the steps overlap and
+// every task is short:
 //
-//  * bulk work -- y_c := y_c - A_{c,i} x_i for every 32-row chunk c that lies
-//    at least two tiles above tile i -- is a queue of (chunk, tile) tasks,
-//    one warp each, taken in order of i; a task computes its product as soon
-//    as x_i is published and applies it to y_c when the chunk's earlier
-//    updates (tiles N..i+1) are in, so every y_c receives its terms in the
-//    same order in every run (deterministic);
-//  * critical work -- the step from x_i to x_{i-1}: the update of tile i-1's
-//    rows by x_i and the product x_{i-1} = U_{i-1}^{-1} y_{i-1} -- runs on a
-//    few reserved SMs (one warp per SM sub-partition, so each has its FP64
-//    pipe to itself), with the k range of both products split into slices of
-//    kBsSlice columns over many warps; the last warp to finish a chunk adds
-//    the slices' partial sums in slice order.
+//  * the rows are cut into 32-row chunks (one row per lane, coalesced reads
+//    of R's columns) and every tile's columns into S slices of kBsSlice
+//    columns; every (chunk c, slice s) keeps a running sum acc[c][s] of its
+//    terms sum_k R(c, k) x_k over the tiles met so far;
+//  * bulk tasks (c, i, s) -- chunks at least two tiles above tile i -- come
+//    from one queue in order of i, then c downwards, then s: a task computes
+//    its kBsSlice-column product as soon as x_i is published and adds it to
+//    acc[c][s] once the tiles N..i+1 are in (the turn counter of (c, s)), so
+//    every sum is formed in the same order in every run (deterministic);
+//  * the critical chain x_i -> x_{i-1} runs on a few reserved SMs (the other
+//    blocks on them stay idle, so each critical warp has an FP64 pipe of its
+//    own): the slices of tile i-1's rows times x_i join their running sums,
+//    the last slice of a chunk forms y_c - sum_s acc[c][s], then
+//    x_{i-1} = U_{i-1}^{-1} y_{i-1} in slices whose partial sums the last one
+//    adds in slice order.  Each of these chains is bound by the latency of
+//    one warp's md operations (about three times their issue time on GB300:
+//    8 qd md FMAs take 33 us, 16 md additions 45 us); two interleaved chains
+//    per warp or operands loaded ahead in registers measured slower.
 //
-// Every wait is bounded (wait_ge): a wait that runs out records
-// MDLS_ERR_TIMEOUT and every warp leaves at its next wait or task.
-// Data written by other SMs is read with ld.global.cg (L2), never from L1.
+// Every wait is bounded (warp_wait_ge): a wait that runs out records
+// MDLS_ERR_TIMEOUT and every warp leaves at its next wait or task.  Data
+// written by other SMs is read with ld.global.cg (L2), never from L1.
 #pragma once
 #include "kernels.cuh"
+#include "layout.h"
 
 namespace mdls {
 
-constexpr int kBsSlice = 8;       // columns per slice of the critical products
-constexpr int kBsCritSms = 16;    // SMs reserved for the critical path
-constexpr int kBsMaxSm = 1024;    // slots of the per-SM role claim
+constexpr int kBsSlice = kBsSliceCols;  // columns per slice
+constexpr int kBsCritSms = 16;          // SMs reserved for the critical chain
+constexpr int kBsBlocksPerSm = 3;       // 128-thread blocks per SM: three warps per sub-partition
+constexpr int kBsMaxSm = 1024;          // slots of the per-SM role claim
 
-// Counters of the persistent back substitution (unsigned ints, zeroed by the
-// host before the launch).
+// Counters (unsigned ints, zeroed by the host before the launch).
 struct BsCtr {
-    int64_t bulk_head, crit_head, crit_claims, sm_claim, sm_slot, bulk_done, cu_cnt, xt_cnt, yfin, xready, total;
-    __host__ __device__ static BsCtr make(int64_t nchunks, int64_t N) {
+    int64_t bulk_head, crit_head, crit_claims, sm_role, sm_slot, turn, cu_cnt, xt_cnt, yfin, xready, total;
+    __host__ __device__ static BsCtr make(int64_t nchunks, int64_t S, int64_t N) {
         BsCtr c;
         c.bulk_head = 0;
         c.crit_head = 32;   // separate 128-byte lines for the queue heads
         c.crit_claims = 64;
-        c.sm_claim = 96;
-        c.sm_slot = c.sm_claim + kBsMaxSm;
-        c.bulk_done = c.sm_slot + kBsMaxSm;
-        c.cu_cnt = c.bulk_done + nchunks;
-        c.xt_cnt = c.cu_cnt + nchunks;
-        c.yfin = c.xt_cnt + nchunks;
-        c.xready = c.yfin + N;
-        c.total = c.xready + N;
+        c.sm_role = 96;
+        c.sm_slot = c.sm_role + kBsMaxSm;
+        c.turn = c.sm_slot + kBsMaxSm;   // (chunk, slice): bulk tiles added to acc
+        c.cu_cnt = c.turn + nchunks * S;  // chunk: critical slices added
+        c.xt_cnt = c.cu_cnt + nchunks;    // chunk: slices of x = U^{-1} y done
+        c.yfin = c.xt_cnt + nchunks;      // tile: chunks whose y is final
+        c.xready = c.yfin + N;            // tile: chunks of x published
+        c.total = c.xready + N;           // == bs_ctr_ints(nchunks, S, N)
         return c;
     }
 };
@@ -62,9 +71,9 @@ struct BsPersistArgs {
     double* yb;          // working right-hand side, P planes of n
     double* x;
     int64_t psx;
-    double* cu_part;     // [limb][chunk][slice][lane] partial sums of the critical updates
+    double* acc;         // [limb][chunk][slice][lane] running sums of the updates
     double* xt_part;     // [limb][chunk][slice][lane] partial sums of x = U^{-1} y
-    int64_t part_ps;     // plane stride of the partial-sum buffers
+    int64_t part_ps;     // plane stride of acc and xt_part
     unsigned int* ctr;
     int64_t n;
     int t, N, nchunks, S, KS, ncrit;
@@ -92,7 +101,7 @@ DEV_INLINE bool warp_wait_ge(const unsigned int* c, unsigned int want, WsHeader*
                     ok = 0;
                     break;
                 }
-                __nanosleep(100);
+                __nanosleep(64);
             }
         }
         __threadfence();
@@ -129,8 +138,8 @@ DEV_INLINE int tile_width(int64_t n, int t, int64_t j) {
 
 // sum_{k in [k0, k1)} A(r, k) x_k with lanes on rows (A column-major, coalesced)
 template <int P>
-DEV_INLINE md<P> rows_times_x(const double* A, int64_t lda, int64_t psa, int64_t r, bool rv, int64_t k0,
-                              int64_t k1, const double* x, int64_t psx) {
+DEV_INLINE md<P> rows_times_x(const double* A, int64_t lda, int64_t psa, int64_t r, int64_t k0, int64_t k1,
+                              const double* x, int64_t psx) {
     double bins[P];
 #pragma unroll
     for (int l = 0; l < P; ++l) bins[l] = 0.0;
@@ -139,7 +148,7 @@ DEV_INLINE md<P> rows_times_x(const double* A, int64_t lda, int64_t psa, int64_t
         md<P> a, xv;
 #pragma unroll
         for (int l = 0; l < P; ++l) {
-            a.v[l] = rv ? A[l * psa + k * lda + r] : 0.0;
+            a.v[l] = A[l * psa + k * lda + r];
             xv.v[l] = __ldcg(x + l * psx + k);
         }
         md_fma_bins<P>(bins, a, xv);
@@ -148,14 +157,27 @@ DEV_INLINE md<P> rows_times_x(const double* A, int64_t lda, int64_t psa, int64_t
     return md_from_bins<P>(bins);
 }
 
-// Number of slices of tile j's columns that meet rows [32 cl, 32 cl + 32) of
-// the upper triangular U_j^{-1} (slices wholly left of the chunk's diagonal
-// are zero) and lie inside the tile.
-DEV_INLINE int xt_needed(int cl, int tt, int S) {
-    int cnt = 0;
-    for (int s = 0; s < S; ++s)
-        if (s * kBsSlice < tt && s * kBsSlice + kBsSlice - 1 >= 32 * cl) ++cnt;
-    return cnt;
+// Columns [k0, k1) of slice s of tile i (empty beyond a ragged last tile).
+DEV_INLINE void slice_cols(int64_t n, int t, int i, int s, int64_t& k0, int64_t& k1) {
+    const int64_t kend = (int64_t)i * t + tile_width(n, t, i);
+    k0 = (int64_t)i * t + (int64_t)s * kBsSlice;
+    k1 = k0 + kBsSlice;
+    if (k1 > kend) k1 = kend;
+    if (k0 > k1) k0 = k1;
+}
+
+// Slices of tile j's columns that meet rows [32 cl, 32 cl + 32) of the upper
+// triangular U_j^{-1} (slices wholly left of the chunk's diagonal are zero)
+// and lie inside the tile of width tt.
+DEV_INLINE bool xt_slice_needed(int cl, int s, int tt) {
+    return s * kBsSlice < tt && s * kBsSlice + kBsSlice - 1 >= 32 * cl;
+}
+
+// acc[c][s] := (first ? 0 : acc[c][s]) + v
+template <int P>
+DEV_INLINE void acc_add(double* acc, int64_t ps, int64_t off, bool first, const md<P>& v) {
+    const md<P> r = first ? v : md_add<P>(ld_md_cg<P>(acc, ps, off), v);
+    st_md<P>(acc, ps, off, r);
 }
 
 template <int P>
@@ -163,14 +185,13 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
     __shared__ int role;  // 0 bulk, 1 critical, 2 idle
     const int lane = threadIdx.x & 31;
     unsigned int* ctr = a.ctr;
-    const BsCtr C = BsCtr::make(a.nchunks, a.N);
+    const BsCtr C = BsCtr::make(a.nchunks, a.S, a.N);
     if (threadIdx.x == 0) {
         // the first block on each SM asks for a critical slot; the first
         // ncrit to ask get one, and the other blocks on their SMs stay idle
-        // so that the critical warps have the SM's FP64 pipes to themselves
         unsigned int smid;
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        unsigned int* sm_role = ctr + C.sm_claim + (smid % kBsMaxSm);   // 0 unset, 1 bulk SM, 2 critical SM
+        unsigned int* sm_role = ctr + C.sm_role + (smid % kBsMaxSm);   // 0 unset, 1 bulk SM, 2 critical SM
         unsigned int* sm_slot = ctr + C.sm_slot + (smid % kBsMaxSm);
         const unsigned int slot = atomicAdd(sm_slot, 1u);
         if (slot == 0) {
@@ -184,8 +205,9 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
             int r = -1;
             while (r < 0) {
                 const unsigned int v = *vr;
-                if (v != 0) r = v == 2 ? 2 : 0;
-                else if (globaltimer_ns() - t0 > kWaitDefaultNs) {
+                if (v != 0) {
+                    r = v == 2 ? 2 : 0;
+                } else if (globaltimer_ns() - t0 > kWaitDefaultNs) {
                     atomicExch(&a.hdr->bar_error, 1);
                     set_status(&a.hdr->status, MDLS_ERR_TIMEOUT);
                     r = 2;
@@ -202,8 +224,8 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
 
     if (role == 1) {
         // critical queue: phase 0 = x_{N-1}; then for i = N-1 .. 1, phase
-        // 2(N-1-i)+1 = update of tile i-1's rows by x_i, phase 2(N-1-i)+2 =
-        // x_{i-1}; KS task slots per phase (unused slots are skipped)
+        // 2(N-1-i)+1 = tile i-1's rows times x_i, phase 2(N-1-i)+2 = x_{i-1};
+        // KS task slots per phase (unused slots are skipped)
         const int64_t total = (int64_t)(2 * N - 1) * a.KS;
         for (;;) {
             if (*reinterpret_cast<volatile int*>(&a.hdr->bar_error)) return;
@@ -213,27 +235,25 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
             if ((int64_t)q >= total) return;
             const int phase = (int)(q / a.KS), k = (int)(q % a.KS);
             if (phase % 2 == 1) {
-                // update of tile j = i - 1 (full width) by x_i, slice s of tile i
+                // slice s of tile j = i - 1's chunk cl times x_i
                 const int i = N - 1 - (phase - 1) / 2, j = i - 1;
                 const int cl = k / S, s = k % S;
                 if (cl >= tc) continue;
                 const int64_t c = (int64_t)j * tc + cl;
-                if (!warp_wait_ge(ctr + C.xready + i, (unsigned)((tile_width(n, t, i) + 31) / 32), a.hdr)) return;
                 const int64_t r = c * 32 + lane;
-                int64_t k0 = (int64_t)i * t + (int64_t)s * kBsSlice;
-                int64_t k1 = k0 + kBsSlice;
-                const int64_t kend = (int64_t)i * t + tile_width(n, t, i);
-                if (k1 > kend) k1 = kend;
-                if (k0 > k1) k0 = k1;
-                const md<P> part = rows_times_x<P>(a.R, a.ldr, a.psr, r, true, k0, k1, a.x, a.psx);
-                st_md<P>(a.cu_part, pps, (c * S + s) * 32 + lane, part);
+                if (!warp_wait_ge(ctr + C.xready + i, (unsigned)((tile_width(n, t, i) + 31) / 32), a.hdr)) return;
+                int64_t k0, k1;
+                slice_cols(n, t, i, s, k0, k1);
+                const md<P> part = rows_times_x<P>(a.R, a.ldr, a.psr, r, k0, k1, a.x, a.psx);
+                // after the bulk tiles N-1 .. i+1 of this slice
+                const int nb = N - 1 - i;
+                if (!warp_wait_ge(ctr + C.turn + c * S + s, (unsigned)nb, a.hdr)) return;
+                acc_add<P>(a.acc, pps, (c * S + s) * 32 + lane, nb == 0, part);
                 const unsigned old = warp_publish(ctr + C.cu_cnt + c);
                 if (old != (unsigned)(S - 1)) continue;
-                // last slice of chunk c: wait for its bulk updates (tiles N-1 .. i+1),
-                // then y_c -= slices 0 .. S-1 in order
-                if (!warp_wait_ge(ctr + C.bulk_done + c, (unsigned)(N - 1 - i), a.hdr)) return;
+                // last slice of chunk c: y_c - acc[c][0] - ... - acc[c][S-1]
                 md<P> y = ld_md_cg<P>(a.yb, n, r);
-                for (int s2 = 0; s2 < S; ++s2) y = md_sub<P>(y, ld_md_cg<P>(a.cu_part, pps, (c * S + s2) * 32 + lane));
+                for (int s2 = 0; s2 < S; ++s2) y = md_sub<P>(y, ld_md_cg<P>(a.acc, pps, (c * S + s2) * 32 + lane));
                 st_md<P>(a.yb, n, r, y);
                 warp_publish(ctr + C.yfin + j);
             } else {
@@ -241,8 +261,7 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
                 const int j = N - 1 - phase / 2;
                 const int tt = tile_width(n, t, j);
                 const int cl = k / S, s = k % S;
-                if (cl * 32 >= tt) continue;
-                if (!(s * kBsSlice < tt && s * kBsSlice + kBsSlice - 1 >= 32 * cl)) continue;
+                if (cl * 32 >= tt || !xt_slice_needed(cl, s, tt)) continue;
                 if (j < N - 1 && !warp_wait_ge(ctr + C.yfin + j, (unsigned)tc, a.hdr)) return;
                 const int rl = cl * 32 + lane;  // row within the tile
                 const bool rv = rl < tt;
@@ -265,12 +284,14 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
                 const int64_t c = (int64_t)j * tc + cl;
                 st_md<P>(a.xt_part, pps, (c * S + s) * 32 + lane, md_from_bins<P>(bins));
                 const unsigned old = warp_publish(ctr + C.xt_cnt + c);
-                if (old != (unsigned)(xt_needed(cl, tt, S) - 1)) continue;
+                int need = 0;
+                for (int s2 = 0; s2 < S; ++s2) need += xt_slice_needed(cl, s2, tt) ? 1 : 0;
+                if (old != (unsigned)(need - 1)) continue;
                 // last slice: x = the slices' sum in slice order
                 md<P> xs = md_zero<P>();
                 bool first = true;
                 for (int s2 = 0; s2 < S; ++s2) {
-                    if (!(s2 * kBsSlice < tt && s2 * kBsSlice + kBsSlice - 1 >= 32 * cl)) continue;
+                    if (!xt_slice_needed(cl, s2, tt)) continue;
                     const md<P> v = ld_md_cg<P>(a.xt_part, pps, (c * S + s2) * 32 + lane);
                     xs = first ? v : md_add<P>(xs, v);
                     first = false;
@@ -281,8 +302,8 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
         }
     }
 
-    // bulk queue: tasks (c, i) for i = N-1 .. 2 and chunks c < (i-1) tc in
-    // decreasing order; step a = N-1-i holds (i-1) tc tasks
+    // bulk queue: tasks (c, i, s) for i = N-1 .. 2, chunks c < (i-1) tc in
+    // decreasing order, slices s; step sa = N-1-i holds (i-1) tc S tasks
     int sa = 0;
     int64_t base = 0;  // first task of step sa
     for (;;) {
@@ -290,22 +311,25 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
         unsigned int q = 0;
         if (lane == 0) q = atomicAdd(ctr + C.bulk_head, 1u);
         q = __shfl_sync(0xffffffffu, q, 0);
-        while (sa < N - 2 && (int64_t)q >= base + (int64_t)(N - 2 - sa) * tc) {
-            base += (int64_t)(N - 2 - sa) * tc;
+        while (sa < N - 2 && (int64_t)q >= base + (int64_t)(N - 2 - sa) * tc * S) {
+            base += (int64_t)(N - 2 - sa) * tc * S;
             ++sa;
         }
         if (sa >= N - 2) return;
         const int i = N - 1 - sa;
-        const int64_t c = (int64_t)(i - 1) * tc - 1 - ((int64_t)q - base);
+        const int64_t idx = (int64_t)q - base;
+        const int64_t c = (int64_t)(i - 1) * tc - 1 - idx / S;
+        const int s = (int)(idx % S);
         if (!warp_wait_ge(ctr + C.xready + i, (unsigned)((tile_width(n, t, i) + 31) / 32), a.hdr)) return;
         const int64_t r = c * 32 + lane;
-        const int64_t k0 = (int64_t)i * t, k1 = k0 + tile_width(n, t, i);
-        const md<P> acc = rows_times_x<P>(a.R, a.ldr, a.psr, r, true, k0, k1, a.x, a.psx);
-        // apply in the chunk's fixed order: tiles N-1, N-2, ..., i+1 before i
-        if (!warp_wait_ge(ctr + C.bulk_done + c, (unsigned)(N - 1 - i), a.hdr)) return;
-        const md<P> y = md_sub<P>(ld_md_cg<P>(a.yb, n, r), acc);
-        st_md<P>(a.yb, n, r, y);
-        warp_publish(ctr + C.bulk_done + c);
+        int64_t k0, k1;
+        slice_cols(n, t, i, s, k0, k1);
+        const md<P> part = rows_times_x<P>(a.R, a.ldr, a.psr, r, k0, k1, a.x, a.psx);
+        // add in the slice's fixed order: tiles N-1, N-2, ..., i+1 before i
+        const int nb = N - 1 - i;
+        if (!warp_wait_ge(ctr + C.turn + c * S + s, (unsigned)nb, a.hdr)) return;
+        acc_add<P>(a.acc, pps, (c * S + s) * 32 + lane, nb == 0, part);
+        warp_publish(ctr + C.turn + c * S + s);
     }
 }
 

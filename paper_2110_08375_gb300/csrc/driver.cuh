@@ -7,6 +7,7 @@
 #include "split.cuh"
 #include "layout.h"
 #include "panel_fx.cuh"
+#include "bs_persist.cuh"
 #include "profile.h"
 
 namespace mdls {
@@ -31,15 +32,25 @@ constexpr int fx_block_threads() {
         if (cudaGetLastError() != cudaSuccess) return MDLS_ERR_CUDA; \
     } while (0)
 
+// Per-device values looked up once (the current device's index selects the
+// slot; devices beyond kMaxDev share the last slot's lookup each time).
+constexpr int kMaxDev = 64;
+inline int cur_dev() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev;
+}
+
 inline int sm_count() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
+    static int sms[kMaxDev] = {};
+    const int dev = cur_dev();
+    int v = (dev >= 0 && dev < kMaxDev) ? sms[dev] : 0;
+    if (v == 0) {
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (v <= 0) v = 1;
+        if (dev >= 0 && dev < kMaxDev) sms[dev] = v;
     }
-    return sms;
+    return v;
 }
 
 // Digit slices of the tensor-core split products (precision mode "split").
@@ -542,12 +553,89 @@ int bs_solve(int64_t n, const double* R, int64_t ldr, int64_t psr, const double*
     return MDLS_OK;
 }
 
+// Step 2 in one persistent cooperative launch (csrc/bs_persist.cuh): bulk
+// updates from a task queue on most SMs, the critical step x_i -> x_{i-1} on
+// kBsCritSms reserved SMs.  Needs t a multiple of 32.
+template <int P>
+int bs_solve_persist(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y, int64_t psy,
+                     double* x, int64_t psx, int t, char* ws, const BsLayout& L, WsHeader* hdr,
+                     cudaStream_t st) {
+    const int64_t N = (n + t - 1) / t;
+    const int64_t nchunks = (n + 31) / 32;
+    double* bw = reinterpret_cast<double*>(ws + L.b);
+    for (int l = 0; l < P; ++l)
+        if (cudaMemcpyAsync(bw + l * n, y + l * psy, n * sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            return MDLS_ERR_CUDA;
+    const int S = t / kBsSlice;
+    unsigned int* ctr = reinterpret_cast<unsigned int*>(ws + L.ctr);
+    if (cudaMemsetAsync(ctr, 0, 4 * (size_t)bs_ctr_ints(nchunks, S, N), st) != cudaSuccess) return MDLS_ERR_CUDA;
+    // blocks per SM: kBsBlocksPerSm, or fewer if that many do not fit (the
+    // cooperative launch needs every block resident)
+    static int per_sm_dev[kMaxDev] = {};
+    const int dev = cur_dev();
+    int per_sm = (dev >= 0 && dev < kMaxDev) ? per_sm_dev[dev] : 0;
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, bs_persist_kernel<P>, 128, 0) != cudaSuccess || v < 1)
+            v = 1;
+        per_sm = v < kBsBlocksPerSm ? v : kBsBlocksPerSm;
+        if (dev >= 0 && dev < kMaxDev) per_sm_dev[dev] = per_sm;
+    }
+    BsPersistArgs a;
+    a.R = R;
+    a.ldr = ldr;
+    a.psr = psr;
+    a.D = reinterpret_cast<const double*>(ws + L.D);
+    a.dps = N * (int64_t)t * t;
+    a.yb = bw;
+    a.x = x;
+    a.psx = psx;
+    a.acc = reinterpret_cast<double*>(ws + L.acc);
+    a.xt_part = reinterpret_cast<double*>(ws + L.xt_part);
+    a.part_ps = L.part_ps;
+    a.ctr = ctr;
+    a.n = n;
+    a.t = t;
+    a.N = (int)N;
+    a.nchunks = (int)nchunks;
+    a.S = S;
+    a.KS = (t / 32) * S;
+    a.ncrit = kBsCritSms < sm_count() / 2 ? kBsCritSms : sm_count() / 2;
+    if (a.ncrit < 1) a.ncrit = 1;
+    a.hdr = hdr;
+    StageScope sc(ST_BSUPD, st);
+    void* args[] = {&a};
+    if (cudaLaunchCooperativeKernel((const void*)bs_persist_kernel<P>, dim3((unsigned)(per_sm * sm_count())),
+                                    dim3(128), args, 0, st) != cudaSuccess)
+        return MDLS_ERR_CUDA;
+    return MDLS_OK;
+}
+
+// Schedule of step 2: one launch pair per tile step (the paper's), or the
+// persistent launch (chosen process-wide by mdls_set_backsub_schedule).  The
+// automatic choice follows measurements on GB300: the persistent launch wins
+// in double double from 8 tiles on (n = 1024 to 4096: 5-35 %) and in quad
+// double for n >= 8192 (n = 17920: 41.4 -> 35.2 ms at tile 128), where the
+// overlapped steps outweigh its latency-bound chain x_i -> x_{i-1} (about
+// 150 us per tile step in quad double); octo double stays per step.
+inline bool use_persist(int64_t n, int t, int P) {
+    if (t % 32 != 0) return false;
+    const int s = bs_schedule_ref();
+    if (s == MDLS_BS_PER_STEP) return false;
+    if (s == MDLS_BS_PERSISTENT) return true;
+    if (P == 2) return (n + t - 1) / t >= 8;
+    if (P == 4) return n >= 8192;
+    return false;
+}
+
 template <int P>
 int bs_run(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y, int64_t psy,
            double* x, int64_t psx, int t, char* ws, const BsLayout& L, WsHeader* hdr,
            cudaStream_t st) {
     int rc = bs_invert<P>(n, R, ldr, psr, t, ws, L, hdr, st);
     if (rc) return rc;
+    if (use_persist(n, t, P) && L.ctr != 0) return bs_solve_persist<P>(n, R, ldr, psr, y, psy, x, psx, t, ws, L, hdr, st);
     return bs_solve<P>(n, R, ldr, psr, y, psy, x, psx, t, ws, L, st);
 }
 

@@ -119,3 +119,11 @@ def test_wait_check_argument_errors(L):
     assert L.mdls_wait_check(fake, 512, 10, 0, None) == -1             # limit below 1 us
     assert L.mdls_wait_check(fake, 512, 2 * 10**10, 0, None) == -1     # limit above 10 s
     assert L.mdls_wait_check(fake, 512, 10**6, 2, None) == -1
+
+
+def test_backsub_schedule_argument(L):
+    import paper_2110_08375_gb300 as pkg
+    assert L.mdls_set_backsub_schedule(3) == -1
+    assert L.mdls_set_backsub_schedule(-1) == -1
+    for s in (pkg.BS_PER_STEP, pkg.BS_PERSISTENT, pkg.BS_AUTO):
+        assert L.mdls_set_backsub_schedule(s) == 0

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import TOL, to_dev, to_host
+from gpu_util import TOL, assert_close, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -90,3 +90,61 @@ def test_lstsq_widest_tile(p):
     ws = mdls.mdls_lstsq(to_dev(A), to_dev(b), xd, tile=256)
     assert mdls.mdls_read_status(ws) == 0
     assert oracle.rel_err(to_host(xd), oracle.lstsq(A, b)) < TOL[p]
+
+
+@pytest.fixture
+def schedule():
+    """Sets the back substitution's step-2 schedule for one test and restores
+    the automatic choice afterwards."""
+    import paper_2110_08375_gb300 as mdls
+    yield mdls.mdls_set_backsub_schedule
+    mdls.mdls_set_backsub_schedule(mdls.BS_AUTO)
+
+
+@pytest.mark.parametrize("p", [2, 4, 8])
+@pytest.mark.parametrize("n,tile", [(32, 32), (33, 32), (100, 32), (257, 64), (300, 64), (1000, 128),
+                                    (700, 256)])
+def test_backsub_persistent_schedule_matches_oracle(p, n, tile, schedule):
+    """The persistent launch of step 2 (bulk updates from a task queue, the
+    chain x_i -> x_{i-1} on reserved SMs) against the oracle, with ragged
+    last tiles and one-tile problems; the per-step schedule on the same
+    input agrees with it."""
+    import torch
+    import paper_2110_08375_gb300 as mdls
+    R, y = synth.upper_triangular(p, n, seed=13)
+    Rd, yd = to_dev(R), to_dev(y)
+    xs = {}
+    for sch in (mdls.BS_PERSISTENT, mdls.BS_PER_STEP):
+        schedule(sch)
+        xd = torch.zeros((p, n), dtype=torch.float64, device="cuda")
+        ws = mdls.mdls_backsub(Rd, yd, xd, tile=tile)
+        assert mdls.mdls_read_status(ws) == 0
+        xs[sch] = to_host(xd)
+    xr = oracle.backsub(R, y)
+    assert_close(xs[mdls.BS_PERSISTENT], xr, p, "persistent")
+    assert_close(xs[mdls.BS_PER_STEP], xr, p, "per step")
+
+
+@pytest.mark.parametrize("p", [2, 4, 8])
+def test_lstsq_with_persistent_back_substitution(p, schedule):
+    import torch
+    import paper_2110_08375_gb300 as mdls
+    schedule(mdls.BS_PERSISTENT)
+    m, n = 230, 200
+    A, b = synth.lstsq_problem(p, m, n, seed=14, tag="lspersist")
+    xd = torch.zeros((p, n), dtype=torch.float64, device="cuda")
+    ws = mdls.mdls_lstsq(to_dev(A), to_dev(b), xd, tile=32)
+    assert mdls.mdls_read_status(ws) == 0
+    assert_close(to_host(xd), oracle.lstsq(A, b), p, "lstsq persistent")
+
+
+def test_backsub_persistent_singular_status(schedule):
+    import torch
+    import paper_2110_08375_gb300 as mdls
+    schedule(mdls.BS_PERSISTENT)
+    p, n = 4, 200
+    R, y = synth.upper_triangular(p, n, seed=15)
+    R[:, 150, 150] = 0.0
+    xd = torch.zeros((p, n), dtype=torch.float64, device="cuda")
+    ws = mdls.mdls_backsub(to_dev(R), to_dev(y), xd, tile=32)
+    assert mdls.mdls_read_status(ws) == mdls.MDLS_ERR_SINGULAR

@@ -52,6 +52,43 @@ def test_noalloc_matches_workspace_entry_point_twice():
         assert oracle.rel_err(got, ref) < TOL[p]
 
 
+def test_noalloc_singular_status_and_oracle():
+    """A zero on R's diagonal reaches the caller's status word; a regular
+    problem matches the oracle's row-by-row back substitution."""
+    import torch
+    import oracle
+    mdls, f = _entry()
+    stream = torch.cuda.current_stream()
+    p, n, tile = 2, 90, 32
+    R, y = synth.upper_triangular(p, n, seed=23)
+    for singular in (True, False):
+        Rs = R.copy()
+        if singular:
+            Rs[:, 40, 40] = 0.0
+        Rd, yd = to_dev(Rs), to_dev(y)
+        x = torch.zeros((p, n), dtype=torch.float64, device="cuda")
+        st = torch.full((1,), -99, dtype=torch.int32, device="cuda")
+        rc = f(p, n, Rd.data_ptr(), Rd.stride(1), Rd.stride(0), yd.data_ptr(), yd.stride(0),
+               x.data_ptr(), x.stride(0), tile, st.data_ptr(), C.c_void_p(stream.cuda_stream))
+        assert rc == 0
+        torch.cuda.synchronize()
+        if singular:
+            assert int(st.item()) == mdls.MDLS_ERR_SINGULAR
+        else:
+            assert int(st.item()) == 0
+            assert oracle.rel_err(to_host(x), oracle.backsub(R, y)) < TOL[p]
+
+
+def test_noalloc_size_limits_quoted_in_the_header():
+    """The largest n per precision at tile 128 that the header quotes fits
+    the fixed scratch, and the next size up does not."""
+    mdls, _ = _entry()
+    limit = 16 << 20
+    for p, n in ((2, 6400), (4, 3200), (8, 1536)):
+        assert mdls.mdls_backsub_workspace(p, n, 128) <= limit
+        assert mdls.mdls_backsub_workspace(p, n + 32, 128) > limit
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch():
     import torch
     mdls, f = _entry()
