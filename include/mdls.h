@@ -223,10 +223,11 @@ int mdls_vec_op(int prec, int op, int64_t count, const double* a, int64_t psa, c
  *   when autotune != 0, the autotuner's choice for the size class (prec, n
  *   rounded down to a power of two, the caller's tile if fixed): the first
  *   problem of a class never seen before in this process is solved with each
- *   candidate tile (8, 16, 32; or the caller's) in each mode (plain, split:
- *   the same accuracy) on its own buffers and timed, and the fastest pair
- *   serves the whole class; otherwise the caller's tile or a fixed rule, in
- *   plain mode -- then captures every problem's kernels into one CUDA graph
+ *   candidate tile (8, 16, 32 for n <= 64; 8 .. 64 for n <= 256; 16, 32, 64,
+ *   128 beyond; or the caller's) in each mode (plain, split: the same
+ *   accuracy) on its own buffers, timed three times (median), and the
+ *   fastest pair serves the whole class; otherwise the caller's tile or a
+ *   fixed rule, in plain mode -- then captures every problem's kernels into one CUDA graph
  *   (parallel branches, largest problems first, each problem with its own
  *   slice of ws and a single-block panel) and instantiates it.  Planning
  *   synchronises the device and must not run inside a stream capture.
@@ -260,6 +261,29 @@ int mdls_batched_status(void* plan, int* status, void* stream);
 int mdls_batched_tiles(void* plan, int* tiles);
 int mdls_batched_modes(void* plan, int* modes);
 void mdls_batched_destroy(void* plan);
+
+/*
+ * mdls_lstsq_batched -- the batched least-squares solve in one call, with the
+ * problem array and the per-problem status on the device.
+ *   probs: DEVICE array of count mdls_problem records (device pointers
+ *     inside, as for mdls_batched_plan; tile 0 = autotuned).
+ *   ws: DEVICE workspace of mdls_lstsq_batched_workspace(probs, count) bytes,
+ *     256-byte aligned; it holds every problem's scratch and a table of
+ *     their offsets.
+ *   status: DEVICE int[count]; after the call has run on stream, status[i]
+ *     is problem i's status (MDLS_OK, MDLS_ERR_SINGULAR, MDLS_ERR_TIMEOUT).
+ * The call reads the problem array back to the host (it synchronises
+ * stream once).  The first call for a given batch (same array contents,
+ * workspace, count and device) plans it as mdls_batched_plan does with the
+ * autotuner on, which runs trial solves; the plan is kept in a cache of the
+ * 16 most recent batches, so later calls only launch its graph and a small
+ * status-gathering kernel.  Not for use inside a stream capture.
+ * Returns MDLS_OK, MDLS_ERR_ARG, MDLS_ERR_PREC, MDLS_ERR_WORKSPACE or
+ * MDLS_ERR_CUDA.  mdls_lstsq_batched_workspace returns 0 for an invalid batch.
+ */
+size_t mdls_lstsq_batched_workspace(const mdls_problem* probs, int count);
+int mdls_lstsq_batched(const mdls_problem* probs, int count, void* ws, size_t ws_bytes, int* status,
+                       void* stream);
 
 /*
  * mdls_wait_check -- diagnostic of the bounded device waits (failure

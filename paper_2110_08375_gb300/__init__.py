@@ -86,6 +86,9 @@ def lib() -> C.CDLL:
     L.mdls_batched_modes.argtypes = [vp, C.POINTER(C.c_int)]
     L.mdls_batched_destroy.argtypes = [vp]
     L.mdls_batched_destroy.restype = None
+    L.mdls_lstsq_batched_workspace.argtypes = [vp, C.c_int]
+    L.mdls_lstsq_batched_workspace.restype = sz
+    L.mdls_lstsq_batched.argtypes = [vp, C.c_int, vp, sz, vp, vp]
     L.mdls_vec_op.argtypes = [C.c_int, C.c_int, i64, vp, i64, vp, i64, vp, i64, vp]
     L.mdls_wait_check.argtypes = [vp, sz, C.c_uint64, C.c_int, vp]
     L.mdls_set_backsub_schedule.argtypes = [C.c_int]
@@ -345,3 +348,45 @@ class BatchedPlan:
 
 def mdls_batched_plan(problems, autotune: bool = True) -> BatchedPlan:
     return BatchedPlan(problems, autotune)
+
+
+def problems_device(problems, device=None):
+    """The mdls_problem records of problems [(A, b, x) or (A, b, x, tile)]
+    as a device byte tensor (the layout of include/mdls.h)."""
+    torch = _torch()
+    arr = (Problem * len(problems))()
+    for i, pr in enumerate(problems):
+        A, b, x = pr[:3]
+        tile = pr[3] if len(pr) > 3 else 0
+        for t, nd, nm in ((A, 3, "A"), (b, 2, "b"), (x, 2, "x")):
+            _check_md(t, nd, nm)
+        p, n, lda = A.shape
+        arr[i] = Problem(p, tile, lda, n, A.data_ptr(), A.stride(1), A.stride(0), b.data_ptr(), b.stride(0),
+                         x.data_ptr(), x.stride(0))
+    raw = bytes(memoryview(arr).cast("B"))
+    host = torch.frombuffer(bytearray(raw), dtype=torch.uint8)
+    return host.to(device or problems[0][0].device)
+
+
+def mdls_lstsq_batched(problems, ws=None, status=None, probs_dev=None, stream=None):
+    """Solves every problem with one call (mdls_lstsq_batched): the problem
+    array and the per-problem status live on the device.  Returns
+    (ws, status) -- keep ws (and the problems' tensors) for repeated calls:
+    the library caches the plan of a batch by its contents and workspace."""
+    torch = _torch()
+    if probs_dev is None:
+        probs_dev = problems_device(problems)
+    count = len(problems)
+    if ws is None:
+        need = lib().mdls_lstsq_batched_workspace(probs_dev.data_ptr(), count)
+        if need == 0:
+            raise MdlsError(MDLS_ERR_ARG, "mdls_lstsq_batched_workspace")
+        ws = workspace(need, probs_dev.device)
+    if status is None:
+        status = torch.full((count,), -99, dtype=torch.int32, device=probs_dev.device)
+    rc = lib().mdls_lstsq_batched(probs_dev.data_ptr(), count, ws.data_ptr(), ws.numel() * ws.element_size(),
+                                  status.data_ptr(), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_lstsq_batched")
+    return ws, status
+

@@ -6,17 +6,17 @@
 // problems spread over parallel branches, largest first, each branch fed the
 // next problem when it has the least estimated work -- and instantiates it.
 // Each problem uses the single-block panel (integer digits, one block), so
-// no problem ever waits on blocks of its own that the others keep off the SMs.  mdls_batched_launch()
-// replays the graph on a stream.
+// no problem ever waits on blocks of its own that the others keep off the
+// SMs.  mdls_batched_launch() replays the graph on a stream.
 //
 // Autotuner: for every (precision, n-bucket) class not seen before (n
 // buckets are powers of two), the first problem of that class is solved with
-// each candidate (tile 8, 16, 32 that fit) x (mode plain, split) on the
-// problem's own buffers, timed with CUDA events after one warm-up, and the
-// fastest pair is kept in a process-wide table for every later problem of
-// the class.  Both modes meet the same accuracy; split runs the WY products
-// on the tensor cores and pays for digit conversions, which small problems
-// may not repay.
+// each candidate tile (8, 16, 32 up to n = 64; 8 .. 64 up to n = 256;
+// 16 .. 128 beyond) x (mode plain, split) on the problem's own buffers, timed
+// with CUDA events after one warm-up (median of three), and the fastest pair
+// is kept in a process-wide table for every later problem of the class.
+// Both modes meet the same accuracy; split runs the WY products on the tensor
+// cores and pays for digit conversions, which small problems may not repay.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,9 +42,20 @@ using namespace mdls;
 
 namespace {
 
-const int kCandidates[] = {8, 16, 32};
 const int kModes[] = {MDLS_MODE_PLAIN, MDLS_MODE_SPLIT};
 constexpr int kBranches = 128;  // the device runs at most 128 kernels at once
+constexpr int kTuneReps = 3;    // timings per candidate (median)
+
+// Candidate tiles of the autotuner by problem width.
+struct Cands {
+    int t[4];
+    int count;
+};
+Cands candidates(int64_t n) {
+    if (n <= 64) return Cands{{8, 16, 32, 0}, 3};
+    if (n <= 256) return Cands{{8, 16, 32, 64}, 4};
+    return Cands{{16, 32, 64, 128}, 4};
+}
 
 int solve_one(const mdls_problem& p, int tile, int mode, void* ws, cudaStream_t st) {
     switch (p.prec) {
@@ -68,8 +79,9 @@ size_t problem_ws(const mdls_problem& p) {
             best = std::max(best, ls_layout(p.prec, p.m, p.n, norm_tile(p.tile, p.n), mode == MDLS_MODE_SPLIT).total);
             continue;
         }
-        for (int c : kCandidates) {
-            const int t = norm_tile(c, p.n);
+        const Cands cs = candidates(p.n);
+        for (int q = 0; q < cs.count; ++q) {
+            const int t = norm_tile(cs.t[q], p.n);
             best = std::max(best, ls_layout(p.prec, p.m, p.n, t, mode == MDLS_MODE_SPLIT).total);
         }
     }
@@ -105,19 +117,26 @@ Choice autotune(const mdls_problem& p, void* ws, int* rc) {
     cudaEventCreate(&e1);
     Choice best{p.tile > 0 ? norm_tile(p.tile, p.n) : heuristic_tile(p), MDLS_MODE_PLAIN};
     float best_ms = 1e30f;
+    const Cands cs = candidates(p.n);
     for (int mode : kModes) {
         int last = -1;
-        for (int c : kCandidates) {
-            const int t = p.tile > 0 ? norm_tile(p.tile, p.n) : norm_tile(c, p.n);
+        for (int q = 0; q < cs.count; ++q) {
+            const int t = p.tile > 0 ? norm_tile(p.tile, p.n) : norm_tile(cs.t[q], p.n);
             if (t == last) continue;
             last = t;
-            if (solve_one(p, t, mode, ws, st) != MDLS_OK) continue;
-            float ms = 0.f;
-            cudaEventRecord(e0, st);
-            bool ok = solve_one(p, t, mode, ws, st) == MDLS_OK;
-            cudaEventRecord(e1, st);
-            ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            if (solve_one(p, t, mode, ws, st) != MDLS_OK) continue;  // warm-up
+            float reps[kTuneReps];
+            bool ok = true;
+            for (int r = 0; r < kTuneReps && ok; ++r) {
+                cudaEventRecord(e0, st);
+                ok = solve_one(p, t, mode, ws, st) == MDLS_OK;
+                cudaEventRecord(e1, st);
+                ok = ok && cudaEventSynchronize(e1) == cudaSuccess &&
+                     cudaEventElapsedTime(&reps[r], e0, e1) == cudaSuccess;
+            }
             if (!ok) continue;
+            std::sort(reps, reps + kTuneReps);
+            const float ms = reps[kTuneReps / 2];
             if (ms < best_ms) {
                 best_ms = ms;
                 best = Choice{t, mode};
@@ -299,3 +318,94 @@ void mdls_batched_destroy(void* plan) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// mdls_lstsq_batched: the problem array and the per-problem status live on
+// the device.  The array is read back to plan (a synchronising copy); plans
+// are kept in a small cache keyed by the array's contents, the workspace and
+// the count, so repeated calls on the same batch replay the same graph.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CachedPlan {
+    std::vector<unsigned char> key;
+    void* ws;
+    int dev;
+    Plan* plan;
+    uint64_t* offs;  // device copy of the per-problem workspace offsets (in ws)
+};
+std::mutex g_cache_mu;
+std::vector<CachedPlan> g_cache;  // most recent last
+constexpr size_t kCacheCap = 16;
+
+__global__ void batched_status_kernel(const char* ws, const uint64_t* offs, int count, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) status[i] = *reinterpret_cast<const int*>(ws + offs[i]);
+}
+
+size_t offsets_at(size_t plan_bytes) { return align256(plan_bytes); }
+
+}  // namespace
+
+extern "C" size_t mdls_lstsq_batched_workspace(const mdls_problem* probs, int count) {
+    if (!probs || count < 1) return 0;
+    std::vector<mdls_problem> h((size_t)count);
+    if (cudaMemcpy(h.data(), probs, sizeof(mdls_problem) * (size_t)count, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return 0;
+    const size_t need = mdls_batched_workspace(h.data(), count);
+    if (need == 0) return 0;
+    return offsets_at(need) + align256(sizeof(uint64_t) * (size_t)count);
+}
+
+extern "C" int mdls_lstsq_batched(const mdls_problem* probs, int count, void* ws, size_t ws_bytes, int* status,
+                                  void* stream) {
+    if (!probs || count < 1 || !status) return MDLS_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<mdls_problem> h((size_t)count);
+    if (cudaMemcpyAsync(h.data(), probs, sizeof(mdls_problem) * (size_t)count, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return MDLS_ERR_CUDA;
+    for (int i = 0; i < count; ++i)
+        if (!problem_ok(h[i])) return (h[i].prec == 2 || h[i].prec == 4 || h[i].prec == 8) ? MDLS_ERR_ARG : MDLS_ERR_PREC;
+    const size_t plan_bytes = mdls_batched_workspace(h.data(), count);
+    const size_t need = offsets_at(plan_bytes) + align256(sizeof(uint64_t) * (size_t)count);
+    if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return MDLS_ERR_WORKSPACE;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<unsigned char> key(reinterpret_cast<const unsigned char*>(h.data()),
+                                   reinterpret_cast<const unsigned char*>(h.data()) + sizeof(mdls_problem) * h.size());
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    Plan* P = nullptr;
+    uint64_t* offs = nullptr;
+    for (size_t c = 0; c < g_cache.size(); ++c) {
+        if (g_cache[c].ws == ws && g_cache[c].dev == dev && g_cache[c].key == key) {
+            CachedPlan hit = g_cache[c];
+            g_cache.erase(g_cache.begin() + (long)c);
+            g_cache.push_back(hit);
+            P = hit.plan;
+            offs = hit.offs;
+            break;
+        }
+    }
+    if (!P) {
+        void* handle = nullptr;
+        const int rc = mdls_batched_plan(h.data(), count, ws, plan_bytes, 1, &handle);
+        if (rc != MDLS_OK) return rc;
+        P = static_cast<Plan*>(handle);
+        offs = reinterpret_cast<uint64_t*>(static_cast<char*>(ws) + offsets_at(plan_bytes));
+        std::vector<uint64_t> ho(P->ws_off.begin(), P->ws_off.end());
+        if (cudaMemcpy(offs, ho.data(), sizeof(uint64_t) * ho.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            mdls_batched_destroy(P);
+            return MDLS_ERR_CUDA;
+        }
+        if (g_cache.size() >= kCacheCap) {
+            mdls_batched_destroy(g_cache.front().plan);
+            g_cache.erase(g_cache.begin());
+        }
+        g_cache.push_back(CachedPlan{std::move(key), ws, dev, P, offs});
+    }
+    if (cudaGraphLaunch(P->exec, st) != cudaSuccess) return MDLS_ERR_CUDA;
+    batched_status_kernel<<<(count + 127) / 128, 128, 0, st>>>(P->ws, offs, count, status);
+    return cudaGetLastError() == cudaSuccess ? MDLS_OK : MDLS_ERR_CUDA;
+}
