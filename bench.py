@@ -61,6 +61,12 @@ def parse():
     ap.add_argument("--no-config0", action="store_true")
     ap.add_argument("--no-qr", action="store_true")
     ap.add_argument("--no-modes-large", action="store_true")
+    ap.add_argument("--bs-n", type=int, default=17920, help="size of the back-substitution entry")
+    ap.add_argument("--bs-tile", type=int, default=128)
+    ap.add_argument("--only-backsub", action="store_true",
+                    help="time only the back-substitution entry (a small case for profiling)")
+    ap.add_argument("--bs-sweep", action="store_true",
+                    help="add the back-substitution grid: quad double, n x tile")
     return ap.parse_args()
 
 
@@ -238,6 +244,13 @@ def run_gpu(args):
     precs = [int(x) for x in args.precs.split(",")]
     n, t = args.n, args.tile
     stream = torch.cuda.current_stream()
+    if args.only_backsub:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        res = run_backsub(args, dev, stream, flush, n=args.bs_n, t=args.bs_tile, sweep=False)
+        if rank == 0:
+            print(json.dumps({"backsub": res}), flush=True)
+        barrier(world)
+        return
 
     host = {}
     data = {}
@@ -426,7 +439,9 @@ def run_gpu(args):
     if not args.no_batched:
         out["batched"] = run_batched(args, dev, stream, flush)
     if not args.no_backsub:
-        out["backsub_qd_17920"] = run_backsub(args, dev, stream, flush)
+        out["backsub_qd_17920"] = run_backsub(args, dev, stream, flush, n=args.bs_n, t=args.bs_tile)
+    if args.bs_sweep:
+        out["backsub_sweep_qd"] = run_backsub_sweep(args, dev, stream, flush)
     if not args.no_config0:
         out["lstsq_dd_256"] = run_config0(args, dev, stream, flush)
     if not args.no_qr:
@@ -550,7 +565,7 @@ def cached_oracle(name, *inputs):
     return z["x"] if h.hexdigest() == str(z["input_sha256"]) else None
 
 
-def run_backsub(args, dev, stream, flush, p=4, n=17920, t=128):
+def run_backsub(args, dev, stream, flush, p=4, n=17920, t=128, sweep=True):
     """Back substitution alone (Algorithm 1): quad double, n = 17920, tile 128
     (140 tiles).  R upper triangular with diagonal U[1,2], strict upper part
     U[-1,1)/n, lower limbs x_l = x_(l-1) 2^-54 U[-1,1); y U[-1,1): the seeded
@@ -592,8 +607,8 @@ def run_backsub(args, dev, stream, flush, p=4, n=17920, t=128):
     med = statistics.median(ms)
     # the paper's tile study (its back-substitution experiments vary the tile
     # size at fixed n): the same solve with other tiles, same resident R
-    sweep = {t: med}
-    for t2 in (32, 64, 256):
+    tiles_ms = {t: med}
+    for t2 in ((32, 64, 256) if sweep else ()):
         ws2 = mdls.workspace(mdls.mdls_backsub_workspace(p, n, t2), dev)
         x2 = torch.zeros_like(x)
         mdls.mdls_backsub(R, y, x2, tile=t2, ws=ws2)
@@ -606,7 +621,7 @@ def run_backsub(args, dev, stream, flush, p=4, n=17920, t=128):
             e1.record(stream)
             torch.cuda.synchronize()
             ms2.append(e0.elapsed_time(e1))
-        sweep[t2] = statistics.median(ms2)
+        tiles_ms[t2] = statistics.median(ms2)
         del ws2
     flops = opcount.table1_flops(p, opcount.backsub_counts(n))
     # the paper's count for Algorithm 1 also credits the tile inversions
@@ -628,7 +643,7 @@ def run_backsub(args, dev, stream, flush, p=4, n=17920, t=128):
             "ms": med, "table1_tflops": flops / (med / 1e3) / 1e12,
             "paper_equivalent_tflops": paper_pairs * (sig["add"] + sig["mul"]) / (med / 1e3) / 1e12,
             "hbm_gbs_upper_triangle": rbytes / (med / 1e3) / 1e9, "status": status,
-            "tile_sweep_ms": {str(k2): round(v2, 3) for k2, v2 in sorted(sweep.items())},
+            "tile_sweep_ms": {str(k2): round(v2, 3) for k2, v2 in sorted(tiles_ms.items())},
             "stages_ms": {kk: round(v[0] / k, 3) for kk, v in stages.items() if v[0] > 0}}
 
 
@@ -755,6 +770,51 @@ def run_modes_large(args, dev, stream, flush, m=4096, n=2048, t=128):
                                                                                TOL[p])
         out[PREC_NAMES[p]] = res
         del Ad, bd
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_backsub_sweep(args, dev, stream, flush, p=4, nmax=20480):
+    """The paper's back-substitution study on GB300 (its experiments vary
+    the tile size and the number of tiles at fixed precision): quad double,
+    n in {2560, 5120, 10240, 17920, 20480} x tile in {32, 64, 128, 256}, the
+    leading n x n block of one seeded upper triangular R (diagonal U[1,2],
+    strict upper part U[-1,1)/nmax), drawn on the device with torch's
+    generator (timing only: these solves are not compared with the oracle;
+    the n = 17920 entry above is).  Median of three solves, L2 flushed."""
+    import torch
+
+    import paper_2110_08375_gb300 as mdls
+    from paper_2110_08375_gb300 import opcount
+    g = torch.Generator(device=dev)
+    g.manual_seed(1)
+    R = torch.empty((p, nmax, nmax), dtype=torch.float64, device=dev)   # [limb][col][row]
+    R[0].uniform_(-1.0, 1.0, generator=g).div_(nmax)
+    R[0].diagonal().uniform_(1.0, 2.0, generator=g)
+    for l in range(1, p):
+        R[l].uniform_(-1.0, 1.0, generator=g).mul_(R[l - 1]).mul_(2.0 ** -54)
+    for l in range(p):
+        R[l].copy_(torch.tril(R[l]))
+    y = torch.empty((p, nmax), dtype=torch.float64, device=dev)
+    y[0].uniform_(-1.0, 1.0, generator=g)
+    for l in range(1, p):
+        y[l].uniform_(-1.0, 1.0, generator=g).mul_(y[l - 1]).mul_(2.0 ** -54)
+    out = {}
+    for n in (2560, 5120, 10240, 17920, 20480):
+        Rv = R.as_strided((p, n, n), (nmax * nmax, nmax, 1))   # leading n x n block, ld = nmax
+        yv = y[:, :n]
+        row = {}
+        for t in (32, 64, 128, 256):
+            x = torch.zeros((p, n), dtype=torch.float64, device=dev)
+            ws = mdls.workspace(mdls.mdls_backsub_workspace(p, n, t), dev)
+            mdls.mdls_backsub(Rv, yv, x, tile=t, ws=ws)
+            torch.cuda.synchronize()
+            ms = _timed(stream, flush, lambda: mdls.mdls_backsub(Rv, yv, x, tile=t, ws=ws), 3)
+            row[str(t)] = {"ms": round(ms, 3), "status": mdls.mdls_read_status(ws),
+                           "table1_tflops": round(opcount.table1_flops(p, opcount.backsub_counts(n)) / (ms / 1e3) / 1e12, 3)}
+            del ws
+        out[str(n)] = row
+    del R
     torch.cuda.empty_cache()
     return out
 
