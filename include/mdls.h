@@ -38,8 +38,8 @@
  * after the call.
  *
  * PRECISION `prec`: 2, 4 or 8 limbs.  TILE `tile`: tile size t in 1..256 (the
- * paper's n), 0 = default (128 for QR and least squares, 64 for
- * mdls_backsub; the problem size when smaller).  The last
+ * paper's n), 0 = default (128 for QR and least squares; for mdls_backsub
+ * 128 in dd and qd, 64 in od; the problem size when smaller).  The last
  * tile may be narrower than t ("ragged"), so n need not be a multiple of t.
  */
 #ifndef MDLS_H

@@ -64,7 +64,7 @@ size_t mdls_qr_workspace(int prec, int64_t m, int64_t n, int tile, int want_q, i
 }
 
 size_t mdls_backsub_workspace(int prec, int64_t n, int tile) {
-    int t = norm_tile_bs(tile, n);
+    int t = norm_tile_bs(tile, n, prec);
     if (!prec_ok(prec) || t < 1 || n < 1) return 0;
     size_t total = 0;
     bs_layout(prec, n, t, &total);
@@ -105,7 +105,7 @@ int mdls_backsub(int prec, int64_t n, const double* R, int64_t ldr, int64_t psr,
     if (!prec_ok(prec)) return MDLS_ERR_PREC;
     if (!R || !y || !x || n < 1 || ldr < n || psr < ldr * n || psy < n || psx < n)
         return MDLS_ERR_ARG;
-    const int t = norm_tile_bs(tile, n);
+    const int t = norm_tile_bs(tile, n, prec);
     if (t < 1) return MDLS_ERR_ARG;
     if (!ws_ok(ws, ws_bytes, mdls_backsub_workspace(prec, n, tile))) return MDLS_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -186,13 +186,14 @@ inline LsLayout ls_layout(int P, int64_t m, int64_t n, int t, bool split = false
     return L;
 }
 
-// Back substitution alone: tile 0 = 64.  Measured on qd n = 17920: tiles
-// 32, 64, 128, 256 take 74, 67, 74, 103 ms -- narrower tiles halve the tile
-// inversions' work (n t^2 / 6 md FMAs) until the latency of the 2n/t
-// dependent tile steps takes over.
-inline int norm_tile_bs(int tile, int64_t n) {
+// Back substitution alone: tile 0 = 128 in double and quad double, 64 in
+// octo double.  Measured on GB300 (qd, n = 2560 .. 20480, tiles 32 .. 256):
+// tile 128 is fastest at every n (n = 17920: 58.6 / 38.4 / 35.1 / 53.7 ms at
+// tiles 32 / 64 / 128 / 256); in od the tile inversions (n t^2 / 6 md FMAs)
+// dominate and tile 64 is faster (n = 2048: 14.1 against 18.9 ms).
+inline int norm_tile_bs(int tile, int64_t n, int prec) {
     if (tile < 0 || tile > 256) return -1;
-    int t = tile == 0 ? 64 : tile;
+    int t = tile == 0 ? (prec == 8 ? 64 : 128) : tile;
     if (n > 0 && t > n) t = (int)n;
     return t;
 }

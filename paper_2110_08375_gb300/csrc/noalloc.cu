@@ -59,7 +59,7 @@ extern "C" int mdls_backsub_noalloc(int prec, int64_t n, const double* R, int64_
     if (prec != 2 && prec != 4 && prec != 8) return MDLS_ERR_PREC;
     if (!R || !y || !x || n < 1 || ldr < n || psr < ldr * n || psy < n || psx < n)
         return MDLS_ERR_ARG;
-    const int t = mdls::norm_tile_bs(tile, n);
+    const int t = mdls::norm_tile_bs(tile, n, prec);
     if (t < 1) return MDLS_ERR_ARG;
     const size_t need = mdls_backsub_workspace(prec, n, tile);
     if (need == 0 || need > (size_t)MDLS_BACKSUB_NOALLOC_MAX_BYTES) return MDLS_ERR_WORKSPACE;

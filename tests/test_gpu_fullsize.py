@@ -42,11 +42,11 @@ def test_backsub_qd_17920():
     ws = mdls.mdls_backsub(Rd, yd, xd, tile=t)
     assert mdls.mdls_read_status(ws) == 0
     assert_close(to_host(xd), xr, p, "backsub qd n=17920 tile 128")
-    # the default tile as well
+    # tile 64 as well (280 tiles)
     x2 = torch.zeros_like(xd)
-    ws2 = mdls.mdls_backsub(Rd, yd, x2)
+    ws2 = mdls.mdls_backsub(Rd, yd, x2, tile=64)
     assert mdls.mdls_read_status(ws2) == 0
-    assert_close(to_host(x2), xr, p, "backsub qd n=17920 default tile")
+    assert_close(to_host(x2), xr, p, "backsub qd n=17920 tile 64")
 
 
 @pytest.mark.parametrize("p", [4, 8])
