@@ -66,6 +66,9 @@ def lib():
         L.mdref_gemv.argtypes = [C.c_int, C.c_int, i64, i64, _dp, i64, i64, _dp, _dp]
         L.mdref_gemm.argtypes = [C.c_int, i64, i64, i64, _dp, i64, i64, _dp, i64, i64, _dp,
                                  i64, i64]
+        L.mdref_zqr.argtypes = [C.c_int, i64, i64, _dp, _dp, i64, i64, _dp, _dp, i64, i64, _dp]
+        L.mdref_zbacksub.argtypes = [C.c_int, i64, _dp, _dp, i64, i64, _dp, _dp, _dp, _dp]
+        L.mdref_zlstsq.argtypes = [C.c_int, i64, i64, _dp, _dp, i64, i64, _dp, _dp, _dp, _dp]
         _lib = L
     return _lib
 
@@ -200,6 +203,54 @@ def lstsq(A, b):
     if rc:
         raise ValueError(f"mdref_lstsq failed: {rc}")
     return x
+
+
+def zqr(Ar, Ai, want_q: bool = True):
+    """Complex Householder QR (Hermitian reflectors, diag(R) = phase(x0) ||x||).
+    Ar, Ai: (p, n, m) limb-planar real and imaginary parts.  Returns
+    (Rr, Ri, Qr, Qi, beta) with Q None when want_q is False."""
+    Ar, Ai = _md(Ar).copy(), _md(Ai).copy()
+    p, n, m = Ar.shape
+    Qr = np.zeros((p, m, m)) if want_q else None
+    Qi = np.zeros((p, m, m)) if want_q else None
+    beta = np.zeros((p, n))
+    rc = lib().mdref_zqr(p, m, n, _ptr(Ar), _ptr(Ai), m, n * m, _ptr(Qr) if want_q else None,
+                         _ptr(Qi) if want_q else None, m, m * m, _ptr(beta))
+    if rc:
+        raise ValueError(f"mdref_zqr failed: {rc}")
+    return Ar, Ai, Qr, Qi, beta
+
+
+def zbacksub(Rr, Ri, yr, yi):
+    """Solves R x = y for complex upper triangular R (re/im planes (p, n, ld))."""
+    Rr, Ri, yr, yi = _md(Rr), _md(Ri), _md(yr), _md(yi)
+    p, n, ld = Rr.shape
+    xr, xi = np.zeros((p, n)), np.zeros((p, n))
+    rc = lib().mdref_zbacksub(p, n, _ptr(Rr), _ptr(Ri), ld, n * ld, _ptr(yr), _ptr(yi), _ptr(xr), _ptr(xi))
+    if rc:
+        raise ZeroDivisionError("zero diagonal entry in R")
+    return xr, xi
+
+
+def zlstsq(Ar, Ai, br, bi):
+    """Complex least squares: min ||b - A x|| (unblocked complex Householder QR of [A | b])."""
+    Ar, Ai, br, bi = _md(Ar), _md(Ai), _md(br), _md(bi)
+    p, n, m = Ar.shape
+    xr, xi = np.zeros((p, n)), np.zeros((p, n))
+    rc = lib().mdref_zlstsq(p, m, n, _ptr(Ar), _ptr(Ai), m, n * m, _ptr(br), _ptr(bi), _ptr(xr), _ptr(xi))
+    if rc == -2:
+        raise ZeroDivisionError("zero diagonal entry in R")
+    if rc:
+        raise ValueError(f"mdref_zlstsq failed: {rc}")
+    return xr, xi
+
+
+def zrel_err(xr, xi, rr, ri) -> float:
+    """||x - ref|| / ||ref|| for complex md arrays, differences formed exactly."""
+    dr, di = diff(xr, rr), diff(xi, ri)
+    nr = float(np.sqrt(np.sum(_md(rr)[0] ** 2) + np.sum(_md(ri)[0] ** 2)))
+    nd = float(np.sqrt(np.sum(dr ** 2) + np.sum(di ** 2)))
+    return nd / nr if nr else nd
 
 
 def gemv(A, x, trans: bool = False):

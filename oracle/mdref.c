@@ -659,3 +659,302 @@ void mdref_gemm(int p, int64_t m, int64_t n, int64_t k, const double *Ap, int64_
     store_planar(p, m, n, MC, Cp, ldc, psc);
     free(MA); free(MB); free(MC);
 }
+
+/* ------------------------------------------------------------------------
+ * Complex multiple doubles (the paper's remark in Section 3: on complex data
+ * the transpose becomes the Hermitian transpose; real and imaginary parts
+ * are kept separately, Section 2).  A complex md value is 2p contiguous
+ * doubles in element-major work arrays: the p limbs of the real part, then
+ * the p limbs of the imaginary part.  Each part of a sum or product is
+ * formed exactly and rounded once.
+ * ---------------------------------------------------------------------- */
+#define ZEL(M, r, i, j, p) ((M) + (((size_t)(j) * (size_t)(r)) + (size_t)(i)) * (size_t)(2 * (p)))
+
+static void z_zero(int p, double *c) { md_zero(2 * p, c); }
+
+static void z_add(acc_t *A, cnt_t *K, int p, const double *a, const double *b, double *c) {
+    md_add(A, K, p, a, b, c);
+    md_add(A, K, p, a + p, b + p, c + p);
+}
+
+static void z_sub(acc_t *A, cnt_t *K, int p, const double *a, const double *b, double *c) {
+    md_sub(A, K, p, a, b, c);
+    md_sub(A, K, p, a + p, b + p, c + p);
+}
+
+/* c = (conj(a) if ca) * b, each part exact then rounded; c may alias a or b */
+static void z_mul_opt(acc_t *A, cnt_t *K, int p, const double *a, int ca, const double *b, double *c) {
+    double re[MAXP], im[MAXP];
+    const double sa = ca ? -1.0 : 1.0;
+    acc_clear(A);
+    for (int i = 0; i < p; i++)
+        for (int j = 0; j < p; j++) {
+            acc_add_prod(A, a[i], b[j]);
+            acc_add_prod(A, -sa * a[p + i], b[p + j]);
+        }
+    acc_round_to(A, p, re);
+    acc_clear(A);
+    for (int i = 0; i < p; i++)
+        for (int j = 0; j < p; j++) {
+            acc_add_prod(A, a[i], b[p + j]);
+            acc_add_prod(A, sa * a[p + i], b[j]);
+        }
+    acc_round_to(A, p, im);
+    md_copy(p, re, c);
+    md_copy(p, im, c + p);
+    K->c[1] += 4;
+    K->c[0] += 2;
+}
+
+static void z_mul(acc_t *A, cnt_t *K, int p, const double *a, const double *b, double *c) {
+    z_mul_opt(A, K, p, a, 0, b, c);
+}
+
+/* |a|^2 = re^2 + im^2, exact then rounded (real, p limbs) */
+static void z_abs2(acc_t *A, cnt_t *K, int p, const double *a, double *c) {
+    acc_clear(A);
+    for (int i = 0; i < p; i++)
+        for (int j = 0; j < p; j++) {
+            acc_add_prod(A, a[i], a[j]);
+            acc_add_prod(A, a[p + i], a[p + j]);
+        }
+    acc_round_to(A, p, c);
+    K->c[1] += 2;
+    K->c[0] += 1;
+}
+
+/* a / b = (a conj(b)) / |b|^2: numerator and denominator each exact then
+ * rounded, then two md divisions */
+static void z_div(acc_t *A, cnt_t *K, int p, const double *a, const double *b, double *c) {
+    double num[2 * MAXP], den[MAXP];
+    double re[MAXP], im[MAXP];
+    acc_clear(A);
+    for (int i = 0; i < p; i++)
+        for (int j = 0; j < p; j++) {
+            acc_add_prod(A, a[i], b[j]);
+            acc_add_prod(A, a[p + i], b[p + j]);
+        }
+    acc_round_to(A, p, num);
+    acc_clear(A);
+    for (int i = 0; i < p; i++)
+        for (int j = 0; j < p; j++) {
+            acc_add_prod(A, a[p + i], b[j]);
+            acc_add_prod(A, -a[i], b[p + j]);
+        }
+    acc_round_to(A, p, num + p);
+    z_abs2(A, K, p, b, den);
+    md_div(A, K, p, num, den, re);
+    md_div(A, K, p, num + p, den, im);
+    md_copy(p, re, c);
+    md_copy(p, im, c + p);
+}
+
+static int z_is_zero(int p, const double *a) { return md_is_zero(2 * p, a); }
+
+/* Complex Householder vector of x (length L): H = I - beta v v^H with v(0) = 1
+ * and beta real, H x = rho e1 with rho = e^{i theta} ||x||, theta = arg x(0)
+ * (theta = 0 when x(0) = 0).  With sigma = sum_{i>0} |x_i|^2,
+ * mu = sqrt(|x0|^2 + sigma): v0 = x0 - rho = -e^{i theta} sigma / (|x0| + mu)
+ * (no cancellation), v = x / v0, beta = 2 |v0|^2 / (sigma + |v0|^2).
+ * sigma = 0: H = I (beta = 0, v = e1) and rho = x0.  This is Golub and Van
+ * Loan's Alg. 5.1.1 with the sign of the real case replaced by the phase of
+ * x0, so that H is Hermitian and the diagonal of R carries the phases of the
+ * leading entries. */
+static void zhouse(acc_t *A, cnt_t *K, int p, int64_t L, const double *x, double *v,
+                   double *beta, double *rho) {
+    double sigma[MAXP], t[MAXP], a2[MAXP], mu[MAXP], ax[MAXP], den[MAXP], q[MAXP];
+    double v0[2 * MAXP], ph[2 * MAXP], v0a2[MAXP];
+    md_zero(p, sigma);
+    for (int64_t i = 1; i < L; i++) {
+        z_abs2(A, K, p, x + i * 2 * p, t);
+        md_add(A, K, p, sigma, t, sigma);
+    }
+    z_zero(p, v);
+    v[0] = 1.0;
+    if (md_is_zero(p, sigma)) {
+        for (int64_t i = 1; i < L; i++) z_zero(p, v + i * 2 * p);
+        md_zero(p, beta);
+        md_copy(2 * p, x, rho);
+        K->c[5]++;
+        return;
+    }
+    z_abs2(A, K, p, x, a2);
+    md_add(A, K, p, a2, sigma, t);
+    md_sqrt(A, K, p, t, mu);
+    /* phase e^{i theta} = x0 / |x0| (1 when x0 = 0) */
+    z_zero(p, ph);
+    if (md_is_zero(p, a2)) {
+        ph[0] = 1.0;
+        md_zero(p, ax);
+    } else {
+        md_sqrt(A, K, p, a2, ax);
+        md_div(A, K, p, x, ax, ph);
+        md_div(A, K, p, x + p, ax, ph + p);
+    }
+    /* v0 = -ph * sigma / (|x0| + mu) */
+    md_add(A, K, p, ax, mu, den);
+    md_div(A, K, p, sigma, den, q);
+    md_mul(A, K, p, ph, q, v0);
+    md_mul(A, K, p, ph + p, q, v0 + p);
+    md_neg(2 * p, v0, v0);
+    /* beta = 2 |v0|^2 / (sigma + |v0|^2) */
+    z_abs2(A, K, p, v0, v0a2);
+    md_add(A, K, p, sigma, v0a2, den);
+    md_div(A, K, p, v0a2, den, q);
+    for (int k = 0; k < p; k++) beta[k] = 2.0 * q[k];
+    for (int64_t i = 1; i < L; i++) z_div(A, K, p, x + i * 2 * p, v0, v + i * 2 * p);
+    /* rho = ph * mu */
+    md_mul(A, K, p, ph, mu, rho);
+    md_mul(A, K, p, ph + p, mu, rho + p);
+}
+
+/* a <- (I - beta v v^H) a for one column of length L */
+static void zapply_reflector(acc_t *A, cnt_t *K, int p, int64_t L, const double *v,
+                             const double *beta, double *a) {
+    double s[2 * MAXP], t[2 * MAXP], w[2 * MAXP];
+    z_zero(p, s);
+    for (int64_t i = 0; i < L; i++) {
+        z_mul_opt(A, K, p, v + i * 2 * p, 1, a + i * 2 * p, t); /* conj(v_i) a_i */
+        z_add(A, K, p, s, t, s);
+    }
+    md_mul(A, K, p, beta, s, w);
+    md_mul(A, K, p, beta, s + p, w + p);
+    for (int64_t i = 0; i < L; i++) {
+        z_mul(A, K, p, v + i * 2 * p, w, t);
+        z_sub(A, K, p, a + i * 2 * p, t, a + i * 2 * p);
+    }
+}
+
+static void zapply_to_columns(int p, int64_t r, int64_t j, const double *v, const double *beta,
+                              double *M, int64_t c0, int64_t c1) {
+    if (c1 <= c0 || md_is_zero(p, beta)) return;
+    int64_t L = r - j;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(g_threads)
+#endif
+    {
+        acc_t A; acc_init(&A);
+        cnt_t K; memset(&K, 0, sizeof(K));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t c = c0; c < c1; c++)
+            zapply_reflector(&A, &K, p, L, v, beta, ZEL(M, r, j, c, p));
+        cnt_merge(&K);
+    }
+}
+
+static void zqr_unblocked(int p, int64_t m, int64_t n, int64_t nextra, double *M, double *V,
+                          double *B) {
+    acc_t A; acc_init(&A);
+    for (int64_t j = 0; j < n; j++) {
+        int64_t L = m - j;
+        double *x = ZEL(M, m, j, j, p);
+        double *v = ZEL(V, m, j, j, p);
+        double rho[2 * MAXP];
+        zhouse(&A, &g_cnt, p, L, x, v, B + j * p, rho);
+        zapply_to_columns(p, m, j, v, B + j * p, M, j + 1, n + nextra);
+        md_copy(2 * p, rho, x);
+        for (int64_t i = 1; i < L; i++) z_zero(p, x + i * 2 * p);
+    }
+}
+
+/* planar complex (re and im planes) <-> element-major complex */
+static double *zload(int p, int64_t rows, int64_t cols, const double *Xr, const double *Xi,
+                     int64_t ld, int64_t ps) {
+    double *M = (double *)malloc(sizeof(double) * (size_t)2 * p * rows * (cols ? cols : 1) + 8);
+    acc_t A; acc_init(&A);
+    double tmp[MAXP];
+    for (int64_t j = 0; j < cols; j++)
+        for (int64_t i = 0; i < rows; i++) {
+            for (int k = 0; k < p; k++) tmp[k] = Xr[(size_t)k * ps + (size_t)j * ld + i];
+            md_norm(&A, p, tmp, ZEL(M, rows, i, j, p));
+            for (int k = 0; k < p; k++) tmp[k] = Xi[(size_t)k * ps + (size_t)j * ld + i];
+            md_norm(&A, p, tmp, ZEL(M, rows, i, j, p) + p);
+        }
+    return M;
+}
+
+static void zstore(int p, int64_t rows, int64_t cols, const double *M, double *Xr, double *Xi,
+                   int64_t ld, int64_t ps) {
+    for (int64_t j = 0; j < cols; j++)
+        for (int64_t i = 0; i < rows; i++)
+            for (int k = 0; k < p; k++) {
+                Xr[(size_t)k * ps + (size_t)j * ld + i] = ZEL(M, rows, i, j, p)[k];
+                Xi[(size_t)k * ps + (size_t)j * ld + i] = ZEL(M, rows, i, j, p)[p + k];
+            }
+}
+
+int mdref_zqr(int p, int64_t m, int64_t n, double *Ar, double *Ai, int64_t lda, int64_t psa,
+              double *Qr, double *Qi, int64_t ldq, int64_t psq, double *beta) {
+    if (!(p == 2 || p == 4 || p == 8) || m < n || n < 0 || !Ar || !Ai || lda < m) return -1;
+    if ((Qr || Qi) && (!Qr || !Qi || ldq < m)) return -1;
+    double *M = zload(p, m, n, Ar, Ai, lda, psa);
+    double *V = (double *)calloc((size_t)2 * p * m * (n ? n : 1), sizeof(double));
+    double *B = (double *)calloc((size_t)p * (n ? n : 1), sizeof(double));
+    zqr_unblocked(p, m, n, 0, M, V, B);
+    zstore(p, m, n, M, Ar, Ai, lda, psa);
+    if (beta)
+        for (int64_t j = 0; j < n; j++)
+            for (int k = 0; k < p; k++) beta[(size_t)k * n + j] = B[j * p + k];
+    if (Qr) {
+        /* backward accumulation: Q = H_0 (H_1 (... (H_{n-1} I))), each H_j Hermitian */
+        double *Qm = (double *)calloc((size_t)2 * p * m * (m ? m : 1), sizeof(double));
+        for (int64_t i = 0; i < m; i++) ZEL(Qm, m, i, i, p)[0] = 1.0;
+        for (int64_t j = n - 1; j >= 0; j--)
+            zapply_to_columns(p, m, j, ZEL(V, m, j, j, p), B + j * p, Qm, j, m);
+        zstore(p, m, m, Qm, Qr, Qi, ldq, psq);
+        free(Qm);
+    }
+    free(M); free(V); free(B);
+    return 0;
+}
+
+static int zbacksub_em(acc_t *A, int p, int64_t n, const double *R, int64_t rrows,
+                       const double *y, double *x) {
+    double s[2 * MAXP], t[2 * MAXP];
+    for (int64_t i = n - 1; i >= 0; i--) {
+        md_copy(2 * p, y + i * 2 * p, s);
+        for (int64_t j = i + 1; j < n; j++) {
+            z_mul(A, &g_cnt, p, ZEL(R, rrows, i, j, p), x + j * 2 * p, t);
+            z_sub(A, &g_cnt, p, s, t, s);
+        }
+        const double *rii = ZEL(R, rrows, i, i, p);
+        if (z_is_zero(p, rii)) return -2;
+        z_div(A, &g_cnt, p, s, rii, x + i * 2 * p);
+    }
+    return 0;
+}
+
+int mdref_zbacksub(int p, int64_t n, const double *Rr, const double *Ri, int64_t ldr, int64_t psr,
+                   const double *yr, const double *yi, double *xr, double *xi) {
+    if (!(p == 2 || p == 4 || p == 8) || n < 0 || ldr < n) return -1;
+    double *R = zload(p, n, n, Rr, Ri, ldr, psr);
+    double *y = zload(p, n, 1, yr, yi, n, n);
+    double *x = (double *)calloc((size_t)2 * p * (n ? n : 1), sizeof(double));
+    acc_t A; acc_init(&A);
+    int rc = zbacksub_em(&A, p, n, R, n, y, x);
+    zstore(p, n, 1, x, xr, xi, n, n);
+    free(R); free(y); free(x);
+    return rc;
+}
+
+int mdref_zlstsq(int p, int64_t m, int64_t n, const double *Ar, const double *Ai, int64_t lda,
+                 int64_t psa, const double *br, const double *bi, double *xr, double *xi) {
+    if (!(p == 2 || p == 4 || p == 8) || m < n || n < 1 || lda < m) return -1;
+    double *M = (double *)malloc(sizeof(double) * (size_t)2 * p * m * (n + 1));
+    double *MA = zload(p, m, n, Ar, Ai, lda, psa);
+    double *Mb = zload(p, m, 1, br, bi, m, m);
+    memcpy(M, MA, sizeof(double) * (size_t)2 * p * m * n);
+    memcpy(M + (size_t)2 * p * m * n, Mb, sizeof(double) * (size_t)2 * p * m);
+    free(MA); free(Mb);
+    double *V = (double *)calloc((size_t)2 * p * m * n, sizeof(double));
+    double *B = (double *)calloc((size_t)p * n, sizeof(double));
+    zqr_unblocked(p, m, n, 1, M, V, B);
+    double *x = (double *)calloc((size_t)2 * p * n, sizeof(double));
+    acc_t A; acc_init(&A);
+    int rc = zbacksub_em(&A, p, n, M, m, ZEL(M, m, 0, n, p), x);
+    zstore(p, n, 1, x, xr, xi, n, n);
+    free(M); free(V); free(B); free(x);
+    return rc;
+}

@@ -96,6 +96,17 @@ void mdref_gemm(int p, int64_t m, int64_t n, int64_t k, const double *A, int64_t
                 int64_t psa, const double *B, int64_t ldb, int64_t psb, double *C,
                 int64_t ldc, int64_t psc);
 
+/* Complex multiple doubles: real and imaginary parts in separate limb-planar
+ * arrays (re and im pointers, same ld and plane stride).  Householder
+ * reflectors H = I - beta v v^H with beta real and H x = e^{i arg x0} ||x|| e1
+ * (the diagonal of R carries the phases of the leading entries). */
+int mdref_zqr(int p, int64_t m, int64_t n, double *Ar, double *Ai, int64_t lda, int64_t psa,
+              double *Qr, double *Qi, int64_t ldq, int64_t psq, double *beta);
+int mdref_zbacksub(int p, int64_t n, const double *Rr, const double *Ri, int64_t ldr, int64_t psr,
+                   const double *yr, const double *yi, double *xr, double *xi);
+int mdref_zlstsq(int p, int64_t m, int64_t n, const double *Ar, const double *Ai, int64_t lda,
+                 int64_t psa, const double *br, const double *bi, double *xr, double *xi);
+
 #ifdef __cplusplus
 }
 #endif
