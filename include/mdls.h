@@ -192,6 +192,46 @@ int mdls_lstsq(int prec, int64_t m, int64_t n, const double* A, int64_t lda, int
 size_t mdls_lstsq_workspace(int prec, int64_t m, int64_t n, int tile, int mode);
 
 /*
+ * Complex multiple doubles (the paper's Section 3 remark: on complex data the
+ * transpose becomes the Hermitian transpose; Section 2: real and imaginary
+ * parts are kept separately).  Every complex matrix or vector is passed as
+ * two arrays of the layout above, its real part and its imaginary part, with
+ * one leading dimension and one plane stride for both.
+ *
+ * mdls_zqr -- blocked complex Householder QR (Algorithm 2 with Hermitian
+ *   transposes).  Reflectors are Hermitian, H = I - beta v v^H with beta real
+ *   and v(0) = 1, and map the column x to e^{i arg x0} ||x|| e1 (the sign of
+ *   Golub and Van Loan's Alg. 5.1.1 replaced by the phase of x0; x0 = 0 counts
+ *   as phase 0; a column with nothing below x0 is left as it is), so R's
+ *   diagonal carries the phases of the reflected leading entries and R is
+ *   unique for full-rank A.  A (m x n, m >= n) is overwritten by R (strictly
+ *   lower part exactly zero); Q (m x m, both parts, or both NULL) receives
+ *   H_1 ... H_n.  Each tile's WY form is P = I + W Y^H; the trailing update is
+ *   C := C + Y (W^H C).  The WY products run as four real md products each.
+ *   Workspace: mdls_zqr_workspace(prec, m, n, tile, Q != NULL) bytes.
+ * mdls_zbacksub -- Algorithm 1 on a complex upper triangular R (n x n; only
+ *   the upper triangle is read): inverted diagonal tiles, then the tile loop.
+ *   A zero diagonal entry records MDLS_ERR_SINGULAR.  Workspace:
+ *   mdls_zbacksub_workspace(prec, n, tile) bytes.
+ * mdls_zlstsq -- complex least squares min ||b - A x||_2: the complex QR of
+ *   [A | b] (Q^H b by the same updates, no Q formed) and mdls_zbacksub on
+ *   R x = (Q^H b)[0:n].  A and b are read only.  Workspace:
+ *   mdls_zlstsq_workspace(prec, m, n, tile) bytes.
+ * Arguments, tiles, streams and errors as for the real calls.
+ */
+int mdls_zqr(int prec, int64_t m, int64_t n, double* Ar, double* Ai, int64_t lda, int64_t psa, double* Qr,
+             double* Qi, int64_t ldq, int64_t psq, int tile, void* ws, size_t ws_bytes, void* stream);
+size_t mdls_zqr_workspace(int prec, int64_t m, int64_t n, int tile, int want_q);
+int mdls_zbacksub(int prec, int64_t n, const double* Rr, const double* Ri, int64_t ldr, int64_t psr,
+                  const double* yr, const double* yi, int64_t psy, double* xr, double* xi, int64_t psx, int tile,
+                  void* ws, size_t ws_bytes, void* stream);
+size_t mdls_zbacksub_workspace(int prec, int64_t n, int tile);
+int mdls_zlstsq(int prec, int64_t m, int64_t n, const double* Ar, const double* Ai, int64_t lda, int64_t psa,
+                const double* br, const double* bi, int64_t psb, double* xr, double* xi, int64_t psx, int tile,
+                void* ws, size_t ws_bytes, void* stream);
+size_t mdls_zlstsq_workspace(int prec, int64_t m, int64_t n, int tile);
+
+/*
  * mdls_vec_op -- elementwise multiple-double arithmetic on device vectors
  * (Section 1.1: the md add, mul, div of Table 1, and sqrt):
  *   op MDLS_OP_ADD: c = a + b     MDLS_OP_SUB: c = a - b

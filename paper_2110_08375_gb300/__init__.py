@@ -92,6 +92,16 @@ def lib() -> C.CDLL:
     L.mdls_vec_op.argtypes = [C.c_int, C.c_int, i64, vp, i64, vp, i64, vp, i64, vp]
     L.mdls_wait_check.argtypes = [vp, sz, C.c_uint64, C.c_int, vp]
     L.mdls_set_backsub_schedule.argtypes = [C.c_int]
+    L.mdls_zqr.argtypes = [C.c_int, i64, i64, vp, vp, i64, i64, vp, vp, i64, i64, C.c_int, vp, sz, vp]
+    L.mdls_zqr_workspace.argtypes = [C.c_int, i64, i64, C.c_int, C.c_int]
+    L.mdls_zqr_workspace.restype = sz
+    L.mdls_zbacksub.argtypes = [C.c_int, i64, vp, vp, i64, i64, vp, vp, i64, vp, vp, i64, C.c_int, vp, sz, vp]
+    L.mdls_zbacksub_workspace.argtypes = [C.c_int, i64, C.c_int]
+    L.mdls_zbacksub_workspace.restype = sz
+    L.mdls_zlstsq.argtypes = [C.c_int, i64, i64, vp, vp, i64, i64, vp, vp, i64, vp, vp, i64, C.c_int, vp, sz,
+                              vp]
+    L.mdls_zlstsq_workspace.argtypes = [C.c_int, i64, i64, C.c_int]
+    L.mdls_zlstsq_workspace.restype = sz
     _lib = L
     return L
 
@@ -200,6 +210,73 @@ def mdls_lstsq(A, b, x, rows: int | None = None, tile: int = 0, mode: int = MODE
                           ws.numel() * ws.element_size(), _stream(stream))
     if rc != MDLS_OK:
         raise MdlsError(rc, "mdls_lstsq")
+    return ws
+
+
+def _same_layout(a, b, name):
+    if a.shape != b.shape or a.stride() != b.stride():
+        raise ValueError(f"{name}: real and imaginary parts must have one shape and one layout")
+
+
+def mdls_zqr(Ar, Ai, Qr=None, Qi=None, rows: int | None = None, tile: int = 0, ws=None, stream=None):
+    """In-place complex blocked Householder QR: (Ar, Ai) (p, n, ld) become R
+    (strictly lower part zero); (Qr, Qi) (p, m, ldq) receive Q, or None."""
+    _check_md(Ar, 3, "Ar"); _check_md(Ai, 3, "Ai"); _same_layout(Ar, Ai, "A")
+    p, n, lda = Ar.shape
+    m = lda if rows is None else int(rows)
+    want_q = Qr is not None
+    if want_q:
+        _check_md(Qr, 3, "Qr"); _check_md(Qi, 3, "Qi"); _same_layout(Qr, Qi, "Q")
+    need = int(lib().mdls_zqr_workspace(p, m, n, tile, int(want_q)))
+    if need == 0:
+        raise MdlsError(MDLS_ERR_ARG, "mdls_zqr_workspace")
+    if ws is None:
+        ws = workspace(need, Ar.device)
+    rc = lib().mdls_zqr(p, m, n, Ar.data_ptr(), Ai.data_ptr(), Ar.stride(1), Ar.stride(0),
+                        Qr.data_ptr() if want_q else None, Qi.data_ptr() if want_q else None,
+                        Qr.stride(1) if want_q else 0, Qr.stride(0) if want_q else 0, tile, ws.data_ptr(),
+                        ws.numel() * ws.element_size(), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_zqr")
+    return ws
+
+
+def mdls_zbacksub(Rr, Ri, yr, yi, xr, xi, tile: int = 0, ws=None, stream=None):
+    """Algorithm 1 on complex data: solves R x = y (R: (p, n, ld) parts; y, x: (p, n) parts)."""
+    for t, nd, nm in ((Rr, 3, "Rr"), (Ri, 3, "Ri"), (yr, 2, "yr"), (yi, 2, "yi"), (xr, 2, "xr"), (xi, 2, "xi")):
+        _check_md(t, nd, nm)
+    _same_layout(Rr, Ri, "R"); _same_layout(yr, yi, "y"); _same_layout(xr, xi, "x")
+    p, n, ldr = Rr.shape
+    need = int(lib().mdls_zbacksub_workspace(p, n, tile))
+    if need == 0:
+        raise MdlsError(MDLS_ERR_ARG, "mdls_zbacksub_workspace")
+    if ws is None:
+        ws = workspace(need, Rr.device)
+    rc = lib().mdls_zbacksub(p, n, Rr.data_ptr(), Ri.data_ptr(), Rr.stride(1), Rr.stride(0), yr.data_ptr(),
+                             yi.data_ptr(), yr.stride(0), xr.data_ptr(), xi.data_ptr(), xr.stride(0), tile,
+                             ws.data_ptr(), ws.numel() * ws.element_size(), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_zbacksub")
+    return ws
+
+
+def mdls_zlstsq(Ar, Ai, br, bi, xr, xi, rows: int | None = None, tile: int = 0, ws=None, stream=None):
+    """Complex least squares min ||b - A x|| (A: (p, n, ld) parts; b (p, m), x (p, n) parts)."""
+    for t, nd, nm in ((Ar, 3, "Ar"), (Ai, 3, "Ai"), (br, 2, "br"), (bi, 2, "bi"), (xr, 2, "xr"), (xi, 2, "xi")):
+        _check_md(t, nd, nm)
+    _same_layout(Ar, Ai, "A"); _same_layout(br, bi, "b"); _same_layout(xr, xi, "x")
+    p, n, lda = Ar.shape
+    m = lda if rows is None else int(rows)
+    need = int(lib().mdls_zlstsq_workspace(p, m, n, tile))
+    if need == 0:
+        raise MdlsError(MDLS_ERR_ARG, "mdls_zlstsq_workspace")
+    if ws is None:
+        ws = workspace(need, Ar.device)
+    rc = lib().mdls_zlstsq(p, m, n, Ar.data_ptr(), Ai.data_ptr(), Ar.stride(1), Ar.stride(0), br.data_ptr(),
+                           bi.data_ptr(), br.stride(0), xr.data_ptr(), xi.data_ptr(), xr.stride(0), tile,
+                           ws.data_ptr(), ws.numel() * ws.element_size(), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_zlstsq")
     return ws
 
 

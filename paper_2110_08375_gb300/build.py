@@ -14,7 +14,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmdls.so")
-UNITS = ["api.cu", "profile.cu", "noalloc.cu", "batched.cu", "waitcheck.cu", "mdls_p2.cu", "mdls_p4.cu", "mdls_p8.cu"]
+UNITS = ["api.cu", "profile.cu", "noalloc.cu", "batched.cu", "waitcheck.cu", "mdls_p2.cu", "mdls_p4.cu", "mdls_p8.cu",
+         "mdls_z2.cu", "mdls_z4.cu", "mdls_z8.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC"]
 

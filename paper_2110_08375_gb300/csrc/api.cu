@@ -20,6 +20,16 @@ namespace mdls {
 MDLS_DECLARE(2)
 MDLS_DECLARE(4)
 MDLS_DECLARE(8)
+#define MDLS_DECLARE_Z(P)                                                                                    \
+    int zqr_entry_p##P(int64_t, int64_t, double*, double*, int64_t, int64_t, double*, double*, int64_t,       \
+                       int64_t, int, void*, cudaStream_t);                                                     \
+    int zbs_entry_p##P(int64_t, const double*, const double*, int64_t, int64_t, const double*, const double*, \
+                       int64_t, double*, double*, int64_t, int, void*, cudaStream_t);                         \
+    int zls_entry_p##P(int64_t, int64_t, const double*, const double*, int64_t, int64_t, const double*,       \
+                       const double*, int64_t, double*, double*, int64_t, int, void*, cudaStream_t);
+MDLS_DECLARE_Z(2)
+MDLS_DECLARE_Z(4)
+MDLS_DECLARE_Z(8)
 }  // namespace mdls
 
 using namespace mdls;
@@ -151,6 +161,80 @@ int mdls_vec_op(int prec, int op, int64_t count, const double* a, int64_t psa, c
         case 2: return vec_entry_p2(op, count, a, psa, b, psb, c, psc, st);
         case 4: return vec_entry_p4(op, count, a, psa, b, psb, c, psc, st);
         default: return vec_entry_p8(op, count, a, psa, b, psb, c, psc, st);
+    }
+}
+
+size_t mdls_zqr_workspace(int prec, int64_t m, int64_t n, int tile, int want_q) {
+    const int t = norm_tile(tile, n);
+    if (!prec_ok(prec) || t < 1 || m < n || n < 1) return 0;
+    size_t total = 0;
+    zqr_layout(prec, m, n, t, want_q != 0, &total);
+    return total;
+}
+
+size_t mdls_zbacksub_workspace(int prec, int64_t n, int tile) {
+    const int t = norm_tile_bs(tile, n, prec);
+    if (!prec_ok(prec) || t < 1 || n < 1) return 0;
+    size_t total = 0;
+    zbs_layout(prec, n, t, &total);
+    return total;
+}
+
+size_t mdls_zlstsq_workspace(int prec, int64_t m, int64_t n, int tile) {
+    const int t = norm_tile(tile, n);
+    if (!prec_ok(prec) || t < 1 || m < n || n < 1) return 0;
+    return zls_layout(prec, m, n, t).total;
+}
+
+int mdls_zqr(int prec, int64_t m, int64_t n, double* Ar, double* Ai, int64_t lda, int64_t psa, double* Qr,
+             double* Qi, int64_t ldq, int64_t psq, int tile, void* ws, size_t ws_bytes, void* stream) {
+    if (!prec_ok(prec)) return MDLS_ERR_PREC;
+    if (!Ar || !Ai || n < 1 || m < n || lda < m || psa < lda * n) return MDLS_ERR_ARG;
+    if ((Qr != nullptr) != (Qi != nullptr)) return MDLS_ERR_ARG;
+    if (Qr && (ldq < m || psq < ldq * m)) return MDLS_ERR_ARG;
+    const int t = norm_tile(tile, n);
+    if (t < 1) return MDLS_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, mdls_zqr_workspace(prec, m, n, tile, Qr != nullptr))) return MDLS_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (prec) {
+        case 2: return zqr_entry_p2(m, n, Ar, Ai, lda, psa, Qr, Qi, ldq, psq, t, ws, st);
+        case 4: return zqr_entry_p4(m, n, Ar, Ai, lda, psa, Qr, Qi, ldq, psq, t, ws, st);
+        default: return zqr_entry_p8(m, n, Ar, Ai, lda, psa, Qr, Qi, ldq, psq, t, ws, st);
+    }
+}
+
+int mdls_zbacksub(int prec, int64_t n, const double* Rr, const double* Ri, int64_t ldr, int64_t psr,
+                  const double* yr, const double* yi, int64_t psy, double* xr, double* xi, int64_t psx, int tile,
+                  void* ws, size_t ws_bytes, void* stream) {
+    if (!prec_ok(prec)) return MDLS_ERR_PREC;
+    if (!Rr || !Ri || !yr || !yi || !xr || !xi || n < 1 || ldr < n || psr < ldr * n || psy < n || psx < n)
+        return MDLS_ERR_ARG;
+    const int t = norm_tile_bs(tile, n, prec);
+    if (t < 1) return MDLS_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, mdls_zbacksub_workspace(prec, n, tile))) return MDLS_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (prec) {
+        case 2: return zbs_entry_p2(n, Rr, Ri, ldr, psr, yr, yi, psy, xr, xi, psx, t, ws, st);
+        case 4: return zbs_entry_p4(n, Rr, Ri, ldr, psr, yr, yi, psy, xr, xi, psx, t, ws, st);
+        default: return zbs_entry_p8(n, Rr, Ri, ldr, psr, yr, yi, psy, xr, xi, psx, t, ws, st);
+    }
+}
+
+int mdls_zlstsq(int prec, int64_t m, int64_t n, const double* Ar, const double* Ai, int64_t lda, int64_t psa,
+                const double* br, const double* bi, int64_t psb, double* xr, double* xi, int64_t psx, int tile,
+                void* ws, size_t ws_bytes, void* stream) {
+    if (!prec_ok(prec)) return MDLS_ERR_PREC;
+    if (!Ar || !Ai || !br || !bi || !xr || !xi || n < 1 || m < n || lda < m || psa < lda * n || psb < m ||
+        psx < n)
+        return MDLS_ERR_ARG;
+    const int t = norm_tile(tile, n);
+    if (t < 1) return MDLS_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, mdls_zlstsq_workspace(prec, m, n, tile))) return MDLS_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (prec) {
+        case 2: return zls_entry_p2(m, n, Ar, Ai, lda, psa, br, bi, psb, xr, xi, psx, t, ws, st);
+        case 4: return zls_entry_p4(m, n, Ar, Ai, lda, psa, br, bi, psb, xr, xi, psx, t, ws, st);
+        default: return zls_entry_p8(m, n, Ar, Ai, lda, psa, br, bi, psb, xr, xi, psx, t, ws, st);
     }
 }
 

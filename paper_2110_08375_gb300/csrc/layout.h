@@ -206,4 +206,90 @@ inline int norm_tile(int tile, int64_t n) {
     return t;
 }
 
+// ---------------------------------------------------------------------------
+// Complex md (real and imaginary planes) workspaces.
+// ---------------------------------------------------------------------------
+// Workspace of the complex QR.
+struct ZqrLayout {
+    size_t beta, v0r, v0i, wr, wi, Gr, Gi, Tr, Ti, Xr, Xi, Wr, Wi, Zr, Zi, split;
+    int64_t xcols, wcols, split_cap;
+};
+
+inline ZqrLayout zqr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool want_q, int nextra) {
+    ZqrLayout L;
+    const size_t d = sizeof(double) * (size_t)P;
+    L.beta = B.take(d * t);
+    L.v0r = B.take(d * t);
+    L.v0i = B.take(d * t);
+    L.wr = B.take(d * t);
+    L.wi = B.take(d * t);
+    L.Gr = B.take(d * t * t);
+    L.Gi = B.take(d * t * t);
+    L.Tr = B.take(d * t * t);
+    L.Ti = B.take(d * t * t);
+    L.xcols = n + nextra;
+    if (want_q && m > L.xcols) L.xcols = m;
+    L.Xr = B.take(d * t * (size_t)L.xcols);
+    L.Xi = B.take(d * t * (size_t)L.xcols);
+    L.wcols = want_q ? n : t;
+    L.Wr = B.take(d * (size_t)m * (size_t)L.wcols);
+    L.Wi = B.take(d * (size_t)m * (size_t)L.wcols);
+    L.Zr = B.take(d * t * t);
+    L.Zi = B.take(d * t * t);
+    L.split_cap = 16 * (int64_t)t * t;
+    L.split = B.take(d * (size_t)L.split_cap);
+    return L;
+}
+
+// Workspace of the complex back substitution: the inverted diagonal tiles,
+// the working right-hand side, scratch for the level products and split-K.
+struct ZbsLayout {
+    size_t Dr, Di, br, bi, Zr, Zi, split;
+    int64_t split_cap;
+};
+
+inline ZbsLayout zbs_layout_at(Bump& B, int P, int64_t n, int t) {
+    ZbsLayout L;
+    const size_t d = sizeof(double) * (size_t)P;
+    const int64_t N = (n + t - 1) / t;
+    L.Dr = B.take(d * (size_t)N * t * t);
+    L.Di = B.take(d * (size_t)N * t * t);
+    L.br = B.take(d * (size_t)n);
+    L.bi = B.take(d * (size_t)n);
+    L.Zr = B.take(d * (size_t)t * t);
+    L.Zi = B.take(d * (size_t)t * t);
+    L.split_cap = 16 * (int64_t)t * t > kBsPartCap ? 16 * (int64_t)t * t : kBsPartCap;
+    L.split = B.take(d * (size_t)L.split_cap);
+    return L;
+}
+
+inline ZqrLayout zqr_layout(int P, int64_t m, int64_t n, int t, bool want_q, size_t* total) {
+    Bump B;
+    ZqrLayout L = zqr_layout_at(B, P, m, n, t, want_q, 0);
+    if (total) *total = B.off;
+    return L;
+}
+inline ZbsLayout zbs_layout(int P, int64_t n, int t, size_t* total) {
+    Bump B;
+    ZbsLayout L = zbs_layout_at(B, P, n, t);
+    if (total) *total = B.off;
+    return L;
+}
+struct ZlsLayout {
+    ZqrLayout qr;
+    size_t Ar, Ai;
+    ZbsLayout bs;
+    size_t total;
+};
+inline ZlsLayout zls_layout(int P, int64_t m, int64_t n, int t) {
+    Bump B;
+    ZlsLayout L;
+    L.qr = zqr_layout_at(B, P, m, n, t, false, 1);
+    L.Ar = B.take(sizeof(double) * (size_t)P * (size_t)m * (size_t)(n + 1));
+    L.Ai = B.take(sizeof(double) * (size_t)P * (size_t)m * (size_t)(n + 1));
+    L.bs = zbs_layout_at(B, P, n, t);
+    L.total = B.off;
+    return L;
+}
+
 }  // namespace mdls
