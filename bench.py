@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-config0", action="store_true")
     ap.add_argument("--no-qr", action="store_true")
     ap.add_argument("--no-modes-large", action="store_true")
+    ap.add_argument("--no-complex", action="store_true")
     ap.add_argument("--bs-n", type=int, default=17920, help="size of the back-substitution entry")
     ap.add_argument("--bs-tile", type=int, default=128)
     ap.add_argument("--only-backsub", action="store_true",
@@ -448,6 +449,8 @@ def run_gpu(args):
         out["qr_with_q_1024"] = run_qr_with_q(args, dev, stream, flush, precs)
     if not args.no_modes_large:
         out["modes_4096x2048"] = run_modes_large(args, dev, stream, flush)
+    if not args.no_complex:
+        out["complex"] = run_complex(args, dev, stream, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(448, precs)
@@ -815,6 +818,74 @@ def run_backsub_sweep(args, dev, stream, flush, p=4, nmax=20480):
             del ws
         out[str(n)] = row
     del R
+    torch.cuda.empty_cache()
+    return out
+
+
+# The paper's V100 times for complex double-double QR of 512 x 512 ("all
+# kernels", ms) at 16 x 32, 8 x 64, 4 x 128 and 2 x 256 tiles: context only.
+PAPER_V100_ZQR_DD_512_MS = {32: 97.4, 64: 227.4, 128: 238.5, 256: 420.8}
+
+
+def run_complex(args, dev, stream, flush):
+    """Complex multiple doubles (real and imaginary planes): the paper's
+    complex double-double QR of 512 x 512 with Q formed at four tile sizes,
+    and complex least squares m = n = 512, tile 128, in dd, qd and od with
+    each solution's error against the oracle's cached answer when present.
+    Entries of A and b: real and imaginary parts ~ U[-1,1) in every limb
+    recipe, seed 0."""
+    import torch
+
+    import paper_2110_08375_gb300 as mdls
+    import synth
+    from paper_2110_08375_gb300 import opcount
+    out = {}
+    n = 512
+    A_re, _ = synth.lstsq_problem(2, n, n, seed=0, tag="cplx/re")
+    A_im, _ = synth.lstsq_problem(2, n, n, seed=0, tag="cplx/im")
+    A0r, A0i = torch.from_numpy(A_re).to(dev), torch.from_numpy(A_im).to(dev)
+    qr = {}
+    for t in (32, 64, 128, 256):
+        Ar, Ai = A0r.clone(), A0i.clone()
+        Qr = torch.zeros((2, n, n), dtype=torch.float64, device=dev)
+        Qi = torch.zeros_like(Qr)
+        ws = mdls.workspace(mdls.lib().mdls_zqr_workspace(2, n, n, t, 1), dev)
+
+        def run():
+            Ar.copy_(A0r)
+            Ai.copy_(A0i)
+            mdls.mdls_zqr(Ar, Ai, Qr, Qi, tile=t, ws=ws)
+        run()
+        torch.cuda.synchronize()
+        ms = _timed(stream, flush, run, 3)
+        qr[str(t)] = {"ms": round(ms, 3), "status": mdls.mdls_read_status(ws),
+                      "table1_tflops": round(opcount.zqr_table1_flops(2, n, n) / (ms / 1e3) / 1e12, 3),
+                      "paper_v100_kernel_ms": PAPER_V100_ZQR_DD_512_MS[t]}
+        del ws, Qr, Qi
+    out["zqr_dd_512_with_q"] = qr
+    ls = {}
+    for p in (2, 4, 8):
+        Ar, br = synth.lstsq_problem(p, n, n, seed=0, tag="cplx/ls/re")
+        Ai, bi = synth.lstsq_problem(p, n, n, seed=0, tag="cplx/ls/im")
+        d = [torch.from_numpy(v).to(dev) for v in (Ar, Ai, br, bi)]
+        xr = torch.zeros((p, n), dtype=torch.float64, device=dev)
+        xi = torch.zeros_like(xr)
+        ws = mdls.workspace(mdls.lib().mdls_zlstsq_workspace(p, n, n, 128), dev)
+        run = lambda: mdls.mdls_zlstsq(d[0], d[1], d[2], d[3], xr, xi, tile=128, ws=ws)  # noqa: E731
+        run()
+        torch.cuda.synchronize()
+        ms = _timed(stream, flush, run, 3)
+        entry = {"ms": round(ms, 3), "status": mdls.mdls_read_status(ws),
+                 "table1_tflops": round(opcount.zlstsq_table1_flops(p, n, n) / (ms / 1e3) / 1e12, 3)}
+        ref = cached_oracle(f"zlstsq_n512_p{p}", Ar, Ai, br, bi)
+        if ref is not None:
+            import numpy as np
+            xh = np.concatenate([xr.cpu().numpy(), xi.cpu().numpy()], axis=1)
+            e2, ei = md_errors(xh, ref)
+            entry.update({"vs_oracle_rel_2norm": e2, "vs_oracle_max_entry": ei, "ok": e2 < TOL[p] and ei < TOL[p]})
+        ls[PREC_NAMES[p]] = entry
+        del ws
+    out["zlstsq_512_tile128"] = ls
     torch.cuda.empty_cache()
     return out
 

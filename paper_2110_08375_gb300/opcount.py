@@ -68,6 +68,25 @@ def lstsq_table1_flops(p: int, m: int, n: int) -> int:
     return table1_flops(p, lstsq_counts(m, n))
 
 
+def complex_counts(real: dict) -> dict:
+    """md operations of the complex algorithm from those of the real one:
+    a complex multiplication is 4 md multiplications and 2 md additions, a
+    complex addition 2 md additions, so each real multiply-add of the
+    unblocked algorithm becomes 4 md multiplications and 4 md additions (the
+    paper: complex data take about four times as many operations); the
+    divisions and square roots of the reflectors are counted as in the real
+    algorithm (lower order terms)."""
+    return {"add": 4 * real["add"], "mul": 4 * real["mul"], "div": real["div"], "sqrt": real["sqrt"]}
+
+
+def zqr_table1_flops(p: int, m: int, n: int, want_q: bool = True) -> int:
+    return table1_flops(p, complex_counts(qr_counts(m, n, want_q=want_q)))
+
+
+def zlstsq_table1_flops(p: int, m: int, n: int) -> int:
+    return table1_flops(p, complex_counts(lstsq_counts(m, n)))
+
+
 # ---------------------------------------------------------------------------
 # FP64 cost of one device md operation (csrc/md.cuh)
 # ---------------------------------------------------------------------------

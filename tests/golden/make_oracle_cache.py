@@ -5,13 +5,16 @@ Each entry runs only ``oracle/`` (the plain CPU reference) on inputs drawn by
 inputs it was computed from, so that a test can check that it regenerated the
 very same inputs before it compares against the cache.
 
-    python tests/golden/make_oracle_cache.py [cfg1] [cfg3] [--threads N]
+    python tests/golden/make_oracle_cache.py [cfg1] [cfg3] [zls] [--threads N]
 
 cfg1: least squares m = n = 1024 (A and b as drawn for the n = 1024 workload,
       seed 0) in double double, quad double and octo double: x of the
       unblocked Householder QR of [A | b] followed by back substitution.
 cfg3: back substitution R x = y in quad double, n = 17920 (diagonal U[1,2],
       strict upper part U[-1,1)/n, y U[-1,1), seed 0).
+zls:  complex least squares m = n = 512 (real and imaginary parts of A and b
+      drawn as for the dense workload, seed 0) in dd, qd and od; x is stored
+      as its real and imaginary parts side by side, (p, 2n).
 """
 from __future__ import annotations
 
@@ -63,6 +66,24 @@ def make_cfg1() -> None:
         print(f"cfg1 p={p}: {time.time() - t0:.1f} s", flush=True)
 
 
+def zls_inputs(p: int):
+    import synth
+    Ar, br = synth.lstsq_problem(p, 512, 512, seed=0, tag="cplx/ls/re")
+    Ai, bi = synth.lstsq_problem(p, 512, 512, seed=0, tag="cplx/ls/im")
+    return Ar, Ai, br, bi
+
+
+def make_zls() -> None:
+    import oracle
+    for p in (2, 4, 8):
+        Ar, Ai, br, bi = zls_inputs(p)
+        t0 = time.time()
+        xr, xi = oracle.zlstsq(Ar, Ai, br, bi)
+        np.savez_compressed(path(f"zlstsq_n512_p{p}"), x=np.concatenate([xr, xi], axis=1),
+                            input_sha256=input_hash(Ar, Ai, br, bi))
+        print(f"zls p={p}: {time.time() - t0:.1f} s", flush=True)
+
+
 def make_cfg3() -> None:
     import oracle
     R, y = cfg3_inputs()
@@ -90,8 +111,10 @@ if __name__ == "__main__":
         threads = int(args[args.index("--threads") + 1])
     oracle.set_threads(threads)
     os.makedirs(CACHE, exist_ok=True)
-    which = [a for a in args if a in ("cfg1", "cfg3")] or ["cfg1", "cfg3"]
+    which = [a for a in args if a in ("cfg1", "cfg3", "zls")] or ["cfg1", "cfg3", "zls"]
     if "cfg1" in which:
         make_cfg1()
     if "cfg3" in which:
         make_cfg3()
+    if "zls" in which:
+        make_zls()

@@ -68,3 +68,23 @@ def test_qr_with_q_multitile_tile128(p):
     assert_close(Q, Qr, p, "Q")
     for j in range(n):
         assert R[0, j, j] > 0 and np.all(R[:, j, j + 1:] == 0.0)
+
+
+@pytest.mark.parametrize("p", [2, 4, 8])
+def test_zlstsq_n512_tile128_matches_cached_oracle(p):
+    """Complex least squares at the size of the paper's complex QR study
+    (512 x 512), tile 128, against the complex oracle's cached answer."""
+    import torch
+    import paper_2110_08375_gb300 as mdls
+    entry = cache.load(f"zlstsq_n512_p{p}")
+    assert entry is not None, "oracle cache missing: run tests/golden/make_oracle_cache.py zls"
+    xref, h = entry
+    Ar, Ai, br, bi = cache.zls_inputs(p)
+    assert cache.input_hash(Ar, Ai, br, bi) == h
+    n = 512
+    xr = torch.zeros((p, n), dtype=torch.float64, device="cuda")
+    xi = torch.zeros_like(xr)
+    ws = mdls.mdls_zlstsq(to_dev(Ar), to_dev(Ai), to_dev(br), to_dev(bi), xr, xi, tile=128)
+    assert mdls.mdls_read_status(ws) == 0
+    got = np.concatenate([to_host(xr), to_host(xi)], axis=1)
+    assert_close(got, xref, p, "zlstsq n=512 tile 128")
