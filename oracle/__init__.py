@@ -245,6 +245,24 @@ def zlstsq(Ar, Ai, br, bi):
     return xr, xi
 
 
+def toeplitz_lstsq(J, b):
+    """Block forward substitution of the lower triangular block-Toeplitz
+    system J(t) x(t) = b(t) mod t^{d+1}: x_k = lstsq(J_0, b_k - sum_{i=1}^{k}
+    J_i x_{k-i}) for k = 0..d, every step in md arithmetic (the residual by
+    gemv and elementwise subtraction, each block by the unblocked
+    Householder least squares).  J: (p, d+1, n, m), b: (p, d+1, m); returns
+    x (p, d+1, n)."""
+    J, b = _md(J), _md(b)
+    p, d1, n, m = J.shape
+    x = np.zeros((p, d1, n))
+    for k in range(d1):
+        r = b[:, k].copy()
+        for i in range(1, k + 1):
+            r = _vec_sub(r, gemv(J[:, i], x[:, k - i]))
+        x[:, k] = lstsq(J[:, 0], r)
+    return x
+
+
 def zrel_err(xr, xi, rr, ri) -> float:
     """||x - ref|| / ||ref|| for complex md arrays, differences formed exactly."""
     dr, di = diff(xr, rr), diff(xi, ri)
