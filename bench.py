@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-qr", action="store_true")
     ap.add_argument("--no-modes-large", action="store_true")
     ap.add_argument("--no-complex", action="store_true")
+    ap.add_argument("--no-toeplitz", action="store_true")
     ap.add_argument("--bs-n", type=int, default=17920, help="size of the back-substitution entry")
     ap.add_argument("--bs-tile", type=int, default=128)
     ap.add_argument("--only-backsub", action="store_true",
@@ -451,6 +452,8 @@ def run_gpu(args):
         out["modes_4096x2048"] = run_modes_large(args, dev, stream, flush)
     if not args.no_complex:
         out["complex"] = run_complex(args, dev, stream, flush)
+    if not args.no_toeplitz:
+        out["toeplitz"] = run_toeplitz(args, dev, stream, flush)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(448, precs)
@@ -886,6 +889,37 @@ def run_complex(args, dev, stream, flush):
         ls[PREC_NAMES[p]] = entry
         del ws
     out["zlstsq_512_tile128"] = ls
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_toeplitz(args, dev, stream, flush, n=512, d=8, t=128):
+    """Lower triangular block-Toeplitz solve of a power-series Newton step:
+    J(t) x(t) = b(t) mod t^9 with nine 512 x 512 blocks (entries ~ U[-1,1)
+    per limb recipe, seed 0), tile 128, in dd, qd and od: one QR of J_0,
+    then nine block solves."""
+    import numpy as np
+    import torch
+
+    import paper_2110_08375_gb300 as mdls
+    import synth
+    from paper_2110_08375_gb300 import opcount
+    out = {"workload": f"block-Toeplitz J(t) x(t) = b(t) mod t^{d + 1}, {d + 1} blocks of {n} x {n}, tile {t}"}
+    for p in (2, 4, 8):
+        J = np.stack([synth.md_matrix(p, n, n, 0, f"toebench/J{i}") for i in range(d + 1)], axis=1)
+        b = np.stack([synth.md_vector(p, n, 0, f"toebench/b{k}") for k in range(d + 1)], axis=1)
+        Jd = torch.from_numpy(np.ascontiguousarray(J)).to(dev)
+        bd = torch.from_numpy(np.ascontiguousarray(b)).to(dev)
+        x = torch.zeros((p, d + 1, n), dtype=torch.float64, device=dev)
+        ws = mdls.workspace(mdls.lib().mdls_toeplitz_lstsq_workspace(p, n, n, t), dev)
+        run = lambda: mdls.mdls_toeplitz_lstsq(Jd, bd, x, tile=t, ws=ws)  # noqa: E731
+        run()
+        torch.cuda.synchronize()
+        ms = _timed(stream, flush, run, 3)
+        fl = opcount.table1_flops(p, opcount.toeplitz_counts(n, n, d))
+        out[PREC_NAMES[p]] = {"ms": round(ms, 3), "status": mdls.mdls_read_status(ws),
+                              "table1_tflops": round(fl / (ms / 1e3) / 1e12, 3)}
+        del ws, Jd, bd
     torch.cuda.empty_cache()
     return out
 

@@ -192,6 +192,31 @@ int mdls_lstsq(int prec, int64_t m, int64_t n, const double* A, int64_t lda, int
 size_t mdls_lstsq_workspace(int prec, int64_t m, int64_t n, int tile, int mode);
 
 /*
+ * mdls_toeplitz_lstsq -- lower triangular block-Toeplitz system, the linear
+ * systems of Newton's method on power series that motivate the paper
+ * (Section 1: the diagonal block is the Jacobian at the current point of a
+ * path):  with J(t) = J_0 + J_1 t + ... + J_d t^d (m x n blocks, m >= n) and
+ * b(t) = b_0 + ... + b_d t^d, the coefficients x_0 .. x_d of
+ * J(t) x(t) = b(t) mod t^{d+1} by block forward substitution,
+ *     J_0 x_k = b_k - sum_{i=1}^{k} J_i x_{k-i},   k = 0, ..., d,
+ * each in the least-squares sense with ONE QR of J_0 (Algorithm 2, every
+ * tile's W kept) and Algorithm 1 on its R (diagonal tiles inverted once):
+ * x_k = R^{-1} (Q^T r_k)[0:n].  The paper states this application only as
+ * its motivation; the blocked solve is this library's.
+ *   J: block i, limb l, entry (r, c) at J[l * psj + i * bsj + c * ldj + r]
+ *      (ldj >= m, bsj >= ldj n, psj >= (d + 1) bsj); read only.
+ *   b: block k, limb l, entry r at b[l * psb + k * bsb + r] (bsb >= m,
+ *      psb >= (d + 1) bsb); read only.
+ *   x: block k at x[l * psx + k * bsx + c] (bsx >= n, psx >= (d + 1) bsx).
+ * A zero pivot of J_0's R records MDLS_ERR_SINGULAR.  Workspace:
+ * mdls_toeplitz_lstsq_workspace(prec, m, n, tile) bytes.
+ */
+size_t mdls_toeplitz_lstsq_workspace(int prec, int64_t m, int64_t n, int tile);
+int mdls_toeplitz_lstsq(int prec, int64_t m, int64_t n, int64_t d, const double* J, int64_t ldj, int64_t psj,
+                        int64_t bsj, const double* b, int64_t psb, int64_t bsb, double* x, int64_t psx,
+                        int64_t bsx, int tile, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * Complex multiple doubles (the paper's Section 3 remark: on complex data the
  * transpose becomes the Hermitian transpose; Section 2: real and imaginary
  * parts are kept separately).  Every complex matrix or vector is passed as

@@ -92,6 +92,10 @@ def lib() -> C.CDLL:
     L.mdls_vec_op.argtypes = [C.c_int, C.c_int, i64, vp, i64, vp, i64, vp, i64, vp]
     L.mdls_wait_check.argtypes = [vp, sz, C.c_uint64, C.c_int, vp]
     L.mdls_set_backsub_schedule.argtypes = [C.c_int]
+    L.mdls_toeplitz_lstsq_workspace.argtypes = [C.c_int, i64, i64, C.c_int]
+    L.mdls_toeplitz_lstsq_workspace.restype = sz
+    L.mdls_toeplitz_lstsq.argtypes = [C.c_int, i64, i64, i64, vp, i64, i64, i64, vp, i64, i64, vp, i64, i64,
+                                      C.c_int, vp, sz, vp]
     L.mdls_zqr.argtypes = [C.c_int, i64, i64, vp, vp, i64, i64, vp, vp, i64, i64, C.c_int, vp, sz, vp]
     L.mdls_zqr_workspace.argtypes = [C.c_int, i64, i64, C.c_int, C.c_int]
     L.mdls_zqr_workspace.restype = sz
@@ -210,6 +214,31 @@ def mdls_lstsq(A, b, x, rows: int | None = None, tile: int = 0, mode: int = MODE
                           ws.numel() * ws.element_size(), _stream(stream))
     if rc != MDLS_OK:
         raise MdlsError(rc, "mdls_lstsq")
+    return ws
+
+
+def mdls_toeplitz_lstsq(J, b, x, rows: int | None = None, tile: int = 0, ws=None, stream=None):
+    """Block-Toeplitz power-series solve: J (p, d+1, n, ld) blocks J_0..J_d,
+    b (p, d+1, m), x (p, d+1, n) receives x_0..x_d of J(t) x(t) = b(t) mod
+    t^{d+1} (least squares per block with one QR of J_0)."""
+    import torch
+    for t, nm in ((J, "J"), (b, "b"), (x, "x")):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or t.stride(-1) != 1:
+            raise TypeError(f"{nm} must be a float64 CUDA tensor with contiguous rows")
+    if J.dim() != 4 or b.dim() != 3 or x.dim() != 3:
+        raise ValueError("J must be (p, d+1, n, ld), b (p, d+1, m), x (p, d+1, n)")
+    p, d1, n, ldj = J.shape
+    m = ldj if rows is None else int(rows)
+    need = int(lib().mdls_toeplitz_lstsq_workspace(p, m, n, tile))
+    if need == 0:
+        raise MdlsError(MDLS_ERR_ARG, "mdls_toeplitz_lstsq_workspace")
+    if ws is None:
+        ws = workspace(need, J.device)
+    rc = lib().mdls_toeplitz_lstsq(p, m, n, d1 - 1, J.data_ptr(), J.stride(2), J.stride(0), J.stride(1),
+                                   b.data_ptr(), b.stride(0), b.stride(1), x.data_ptr(), x.stride(0), x.stride(1),
+                                   tile, ws.data_ptr(), ws.numel() * ws.element_size(), _stream(stream))
+    if rc != MDLS_OK:
+        raise MdlsError(rc, "mdls_toeplitz_lstsq")
     return ws
 
 

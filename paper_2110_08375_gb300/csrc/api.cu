@@ -16,7 +16,10 @@ namespace mdls {
     int vec_entry_p##P(int, int64_t, const double*, int64_t, const double*, int64_t, double*,     \
                        int64_t, cudaStream_t);                                                     \
     int ls_refine_entry_p##P(int64_t, int64_t, const double*, int64_t, int64_t, const double*,    \
-                             int64_t, double*, int64_t, int, int, void*, cudaStream_t);
+                             int64_t, double*, int64_t, int, int, void*, cudaStream_t);                  \
+    int toe_entry_p##P(int64_t, int64_t, int64_t, const double*, int64_t, int64_t, int64_t,          \
+                       const double*, int64_t, int64_t, double*, int64_t, int64_t, int, void*,         \
+                       cudaStream_t);
 MDLS_DECLARE(2)
 MDLS_DECLARE(4)
 MDLS_DECLARE(8)
@@ -235,6 +238,30 @@ int mdls_zlstsq(int prec, int64_t m, int64_t n, const double* Ar, const double* 
         case 2: return zls_entry_p2(m, n, Ar, Ai, lda, psa, br, bi, psb, xr, xi, psx, t, ws, st);
         case 4: return zls_entry_p4(m, n, Ar, Ai, lda, psa, br, bi, psb, xr, xi, psx, t, ws, st);
         default: return zls_entry_p8(m, n, Ar, Ai, lda, psa, br, bi, psb, xr, xi, psx, t, ws, st);
+    }
+}
+
+size_t mdls_toeplitz_lstsq_workspace(int prec, int64_t m, int64_t n, int tile) {
+    const int t = norm_tile(tile, n);
+    if (!prec_ok(prec) || t < 1 || m < n || n < 1) return 0;
+    return toe_layout(prec, m, n, t).total;
+}
+
+int mdls_toeplitz_lstsq(int prec, int64_t m, int64_t n, int64_t d, const double* J, int64_t ldj, int64_t psj,
+                        int64_t bsj, const double* b, int64_t psb, int64_t bsb, double* x, int64_t psx,
+                        int64_t bsx, int tile, void* ws, size_t ws_bytes, void* stream) {
+    if (!prec_ok(prec)) return MDLS_ERR_PREC;
+    if (!J || !b || !x || n < 1 || m < n || d < 0 || ldj < m || bsj < ldj * n || psj < bsj * (d + 1) ||
+        bsb < m || psb < bsb * (d + 1) || bsx < n || psx < bsx * (d + 1))
+        return MDLS_ERR_ARG;
+    const int t = norm_tile(tile, n);
+    if (t < 1) return MDLS_ERR_ARG;
+    if (!ws_ok(ws, ws_bytes, mdls_toeplitz_lstsq_workspace(prec, m, n, tile))) return MDLS_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (prec) {
+        case 2: return toe_entry_p2(m, n, d, J, ldj, psj, bsj, b, psb, bsb, x, psx, bsx, t, ws, st);
+        case 4: return toe_entry_p4(m, n, d, J, ldj, psj, bsj, b, psb, bsb, x, psx, bsx, t, ws, st);
+        default: return toe_entry_p8(m, n, d, J, ldj, psj, bsj, b, psb, bsb, x, psx, bsx, t, ws, st);
     }
 }
 

@@ -759,6 +759,65 @@ int ls_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t psa, co
     return bs_run<P>(n, Aw, m, psw, Aw + n * m, psw, x, psx, t, w, L.bs, hdr, st);
 }
 
+// Step 2 with the process-wide schedule (per tile step or one persistent
+// launch), the diagonal tiles already inverted.
+template <int P>
+int bs_solve_sched(int64_t n, const double* R, int64_t ldr, int64_t psr, const double* y, int64_t psy, double* x,
+                   int64_t psx, int t, char* ws, const BsLayout& L, WsHeader* hdr, cudaStream_t st) {
+    if (use_persist(n, t, P) && L.ctr != 0) return bs_solve_persist<P>(n, R, ldr, psr, y, psy, x, psx, t, ws, L, hdr, st);
+    return bs_solve<P>(n, R, ldr, psr, y, psy, x, psx, t, ws, L, st);
+}
+
+// Lower triangular block-Toeplitz system (the linear systems of Newton's
+// method on power series, the motivation of the paper's Section 1): with
+// J(t) = sum_i J_i t^i and b(t) = sum_k b_k t^k, the coefficients x_k of
+// J(t) x(t) = b(t) mod t^{d+1} follow by block forward substitution,
+//   J_0 x_k = b_k - sum_{i=1}^{k} J_i x_{k-i},   k = 0, ..., d,
+// each in the least-squares sense with the one QR of the diagonal block J_0
+// (Algorithm 2, every tile's W kept) and Algorithm 1 on its R (diagonal tiles
+// inverted once): x_k = R^{-1} (Q^T r_k)[0:n].
+template <int P>
+int toe_entry(int64_t m, int64_t n, int64_t d, const double* J, int64_t ldj, int64_t psj, int64_t bsj,
+              const double* b, int64_t psb, int64_t bsb, double* x, int64_t psx, int64_t bsx, int t, void* ws,
+              cudaStream_t st) {
+    const ToeLayout L = toe_layout(P, m, n, t);
+    char* w = static_cast<char*>(ws);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(w);
+    if (cudaMemsetAsync(w, 0, L.qr.flags + L.qr.flag_bytes, st) != cudaSuccess) return MDLS_ERR_CUDA;
+    double* A2 = reinterpret_cast<double*>(w + L.A2);
+    double* r = reinterpret_cast<double*>(w + L.r);
+    const int64_t ps2 = m * n;
+    const size_t vb = sizeof(double);
+    for (int l = 0; l < P; ++l)
+        if (cudaMemcpy2DAsync(A2 + l * ps2, m * vb, J + l * psj, ldj * vb, m * vb, n, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            return MDLS_ERR_CUDA;
+    int rc = qr_run<P>(m, n, 0, A2, m, ps2, nullptr, 0, 0, t, w, L.qr, hdr, false, st, true);
+    if (rc) return rc;
+    rc = bs_invert<P>(n, A2, m, ps2, t, w, L.bs, hdr, st);
+    if (rc) return rc;
+    const double* Wb = reinterpret_cast<const double*>(w + L.qr.W);
+    double* X = reinterpret_cast<double*>(w + L.qr.X);
+    const int64_t psw = L.qr.wcols * m, psX = (int64_t)t * L.qr.xcols;
+    const SplitBuf sb{reinterpret_cast<double*>(w + L.qr.split), L.qr.split_cap};
+    for (int64_t k = 0; k <= d; ++k) {
+        for (int l = 0; l < P; ++l)
+            if (cudaMemcpyAsync(r + l * m, b + l * psb + k * bsb, m * vb, cudaMemcpyDeviceToDevice, st) !=
+                cudaSuccess)
+                return MDLS_ERR_CUDA;
+        for (int64_t i = 1; i <= k; ++i) {  // r -= J_i x_{k-i}
+            rc = launch_gemv<P>(ST_OTHER, st, sb, m, n, ViewDense{J + i * bsj, ldj, psj},
+                                ViewDense{x + (k - i) * bsx, n, psx}, Dense{r, m, m}, true, true);
+            if (rc) return rc;
+        }
+        rc = apply_qt<P>(m, n, t, A2, ps2, Wb, psw, r, m, X, psX, sb, ST_OTHER, st);
+        if (rc) return rc;
+        rc = bs_solve_sched<P>(n, A2, m, ps2, r, m, x + k * bsx, psx, t, w, L.bs, hdr, st);
+        if (rc) return rc;
+    }
+    return MDLS_OK;
+}
+
 template <int P>
 int vec_entry(int op, int64_t count, const double* a, int64_t psa, const double* b, int64_t psb,
               double* c, int64_t psc, cudaStream_t st) {
@@ -904,6 +963,11 @@ int ls_refine_entry(int64_t m, int64_t n, const double* A, int64_t lda, int64_t 
                              const double* b, int64_t psb, double* x, int64_t psx, int t,         \
                              int iters, void* ws, cudaStream_t st) {                              \
         return ls_refine_entry<P>(m, n, A, lda, psa, b, psb, x, psx, t, iters, ws, st);          \
+    }                                                                                             \
+    int toe_entry_p##P(int64_t m, int64_t n, int64_t d, const double* J, int64_t ldj, int64_t psj, \
+                       int64_t bsj, const double* b, int64_t psb, int64_t bsb, double* x, int64_t psx,   \
+                       int64_t bsx, int t, void* ws, cudaStream_t st) {                                 \
+        return toe_entry<P>(m, n, d, J, ldj, psj, bsj, b, psb, bsb, x, psx, bsx, t, ws, st);           \
     }                                                                                             \
     int vec_entry_p##P(int op, int64_t count, const double* a, int64_t psa, const double* b,      \
                        int64_t psb, double* c, int64_t psc, cudaStream_t st) {                    \

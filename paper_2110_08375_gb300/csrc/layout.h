@@ -206,6 +206,26 @@ inline int norm_tile(int tile, int64_t n) {
     return t;
 }
 
+// Lower triangular block-Toeplitz solve: the QR of the diagonal block with
+// every tile's W kept, its inverted diagonal tiles, and the work vector.
+struct ToeLayout {
+    QrLayout qr;
+    size_t A2, r;
+    BsLayout bs;
+    size_t total;
+};
+
+inline ToeLayout toe_layout(int P, int64_t m, int64_t n, int t) {
+    Bump B;
+    ToeLayout L;
+    L.qr = qr_layout_at(B, P, m, n, t, false, 0, true, false);
+    L.A2 = B.take(sizeof(double) * (size_t)P * (size_t)m * (size_t)n);
+    L.r = B.take(sizeof(double) * (size_t)P * (size_t)m);
+    L.bs = bs_layout_at(B, P, n, t);
+    L.total = B.off;
+    return L;
+}
+
 // ---------------------------------------------------------------------------
 // Complex md (real and imaginary planes) workspaces.
 // ---------------------------------------------------------------------------

@@ -68,6 +68,27 @@ def lstsq_table1_flops(p: int, m: int, n: int) -> int:
     return table1_flops(p, lstsq_counts(m, n))
 
 
+def toeplitz_counts(m: int, n: int, d: int) -> dict:
+    """md operations of the block-Toeplitz solve by block forward
+    substitution: the QR of J_0 (no Q), then for every block k = 0..d the
+    residual b_k - sum_{i=1}^{k} J_i x_{k-i} (k m n multiply-adds), Q^T r
+    (the n reflectors applied to one vector: 2L+1 mul and 2L add for a
+    reflector of length L) and the back substitution."""
+    q = qr_counts(m, n, want_q=False)
+    add = mul = 0
+    for j in range(n):
+        L = m - j
+        if L > 1:
+            mul += 2 * L + 1
+            add += 2 * L
+    bs = backsub_counts(n)
+    res = (d * (d + 1) // 2) * m * n
+    blocks = d + 1
+    return {"add": q["add"] + blocks * (add + bs["add"]) + res,
+            "mul": q["mul"] + blocks * (mul + bs["mul"]) + res,
+            "div": q["div"] + blocks * bs["div"], "sqrt": q["sqrt"]}
+
+
 def complex_counts(real: dict) -> dict:
     """md operations of the complex algorithm from those of the real one:
     a complex multiplication is 4 md multiplications and 2 md additions, a

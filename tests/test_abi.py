@@ -127,3 +127,15 @@ def test_backsub_schedule_argument(L):
     assert L.mdls_set_backsub_schedule(-1) == -1
     for s in (pkg.BS_PER_STEP, pkg.BS_PERSISTENT, pkg.BS_AUTO):
         assert L.mdls_set_backsub_schedule(s) == 0
+
+
+def test_toeplitz_argument_errors(L):
+    vp = C.c_void_p
+    fake = vp(1 << 20)
+    ws_bytes = 1 << 30
+    # m < n, negative d, block stride too small, precision
+    assert L.mdls_toeplitz_lstsq(2, 4, 8, 1, fake, 4, 64, 32, fake, 8, 4, fake, 16, 8, 4, fake, ws_bytes, None) == -1
+    assert L.mdls_toeplitz_lstsq(2, 8, 4, -1, fake, 8, 64, 32, fake, 16, 8, fake, 8, 4, 4, fake, ws_bytes, None) == -1
+    assert L.mdls_toeplitz_lstsq(2, 8, 4, 1, fake, 8, 64, 16, fake, 16, 8, fake, 8, 4, 4, fake, ws_bytes, None) == -1
+    assert L.mdls_toeplitz_lstsq(3, 8, 4, 1, fake, 8, 64, 32, fake, 16, 8, fake, 8, 4, 4, fake, ws_bytes, None) == -2
+    assert L.mdls_toeplitz_lstsq(2, 8, 4, 1, fake, 8, 64, 32, fake, 16, 8, fake, 8, 4, 4, None, ws_bytes, None) == -3
