@@ -128,7 +128,7 @@ __host__ __device__ constexpr int gemm_tn() {
 // then applied by split_reduce_kernel).  upper_only skips output tiles that
 // lie entirely below the diagonal (symmetric products).
 template <int P, class AV, class BV>
-__global__ void __launch_bounds__(kGemmTile* gemm_tn<P>())
+__global__ void __launch_bounds__(kGemmTile* gemm_tn<P>(), P == 8 ? 3 : 1)
     gemm_kernel(int64_t M, int64_t N, int64_t K, AV A, BV B, Dense C, int negate, int accumulate,
                 int64_t kchunk, int64_t zstride, int upper_only) {
     constexpr int TN = gemm_tn<P>();
@@ -166,12 +166,22 @@ __global__ void __launch_bounds__(kGemmTile* gemm_tn<P>())
         }
         __syncthreads();
         const int kmax = (int)((kend - k0) < kGemmTile ? (kend - k0) : kGemmTile);
+        // the operands of step kk + 1 are read from shared memory while step
+        // kk runs (the staged tiles are zero beyond kend, so the read ahead
+        // stays inside them)
+        md<P> an, bn;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            an.v[l] = As[l][0][tx];
+            bn.v[l] = Bs[l][ty][0];
+        }
         for (int kk = 0; kk < kmax; ++kk) {
-            md<P> av, bv;
+            const md<P> av = an, bv = bn;
+            const int kn = kk + 1 < kGemmTile ? kk + 1 : kk;
 #pragma unroll
             for (int l = 0; l < P; ++l) {
-                av.v[l] = As[l][kk][tx];
-                bv.v[l] = Bs[l][ty][kk];
+                an.v[l] = As[l][kn][tx];
+                bn.v[l] = Bs[l][ty][kn];
             }
             md_fma_bins<P>(bins, av, bv);
         }

@@ -80,7 +80,11 @@ inline QrLayout qr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool w
     L.X = B.take(d * t * (size_t)L.xcols);
     L.wcols = (want_q || keep_w) ? n : t;
     L.W = B.take(d * (size_t)m * (size_t)L.wcols);
-    L.split_cap = 16 * (int64_t)t * t;   // split-K partial sums, md values per plane
+    // split-K partial sums, md values per plane: room for 8 partial products
+    // of a tile's W^T C (t x xcols), so that a product of one to two waves
+    // can be split into whole waves
+    L.split_cap = 16 * (int64_t)t * t;
+    if (8 * (int64_t)t * L.xcols > L.split_cap) L.split_cap = 8 * (int64_t)t * L.xcols;
     L.split = B.take(d * (size_t)L.split_cap);
     L.tc_as = L.tc_bs = L.tc_ea = L.tc_fb = 0;
     L.tc_as_cap = L.tc_bs_cap = 0;
