@@ -154,7 +154,7 @@ int mdls_set_backsub_schedule(int schedule);
  *   MDLS_BACKSUB_NOALLOC_MAX_BYTES inside the library, held by every GPU that
  *   loads the library until the process exits.  Problems needing more
  *   scratch than that (mdls_backsub_workspace(prec, n, tile) bytes; at tile
- *   128: n <= 6400 in dd, 3200 in qd, 1536 in od) are rejected with
+ *   128: n <= 4960 in dd, 2432 in qd, 1152 in od) are rejected with
  *   MDLS_ERR_WORKSPACE before anything is enqueued.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any

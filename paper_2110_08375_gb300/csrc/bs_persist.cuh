@@ -22,12 +22,13 @@
 //  * the critical chain x_i -> x_{i-1} runs on a few reserved SMs (the other
 //    blocks on them stay idle, so each critical warp has an FP64 pipe of its
 //    own): the slices of tile i-1's rows times x_i join their running sums,
-//    the last slice of a chunk forms y_c - sum_s acc[c][s], then
-//    x_{i-1} = U_{i-1}^{-1} y_{i-1} in slices whose partial sums the last one
-//    adds in slice order.  Each of these chains is bound by the latency of
-//    one warp's md operations (about three times their issue time on GB300:
-//    8 qd md FMAs take 33 us, 16 md additions 45 us); two interleaved chains
-//    per warp or operands loaded ahead in registers measured slower.
+//    the chunk's S running sums are added in a binary tree whose root forms
+//    y_c - sum_s acc[c][s], then x_{i-1} = U_{i-1}^{-1} y_{i-1} in slices
+//    whose partial sums meet in a second tree (tree_up: a fixed order, log2 S
+//    dependent additions).  Each chain is bound by the latency of one warp's
+//    md operations (about three times their issue time on GB300: 8 qd md
+//    FMAs take 33 us, a 16-term sequential sum 45 us); two interleaved chains
+//    per warp or operands loaded ahead measured slower.
 //
 // Every wait is bounded (warp_wait_ge): a wait that runs out records
 // MDLS_ERR_TIMEOUT and every warp leaves at its next wait or task.  Data
@@ -45,7 +46,7 @@ constexpr int kBsMaxSm = 1024;          // slots of the per-SM role claim
 
 // Counters (unsigned ints, zeroed by the host before the launch).
 struct BsCtr {
-    int64_t bulk_head, crit_head, crit_claims, sm_role, sm_slot, turn, cu_cnt, xt_cnt, yfin, xready, total;
+    int64_t bulk_head, crit_head, crit_claims, sm_role, sm_slot, turn, cu_node, xt_node, yfin, xready, total;
     __host__ __device__ static BsCtr make(int64_t nchunks, int64_t S, int64_t N) {
         BsCtr c;
         c.bulk_head = 0;
@@ -54,9 +55,9 @@ struct BsCtr {
         c.sm_role = 96;
         c.sm_slot = c.sm_role + kBsMaxSm;
         c.turn = c.sm_slot + kBsMaxSm;   // (chunk, slice): bulk tiles added to acc
-        c.cu_cnt = c.turn + nchunks * S;  // chunk: critical slices added
-        c.xt_cnt = c.cu_cnt + nchunks;    // chunk: slices of x = U^{-1} y done
-        c.yfin = c.xt_cnt + nchunks;      // tile: chunks whose y is final
+        c.cu_node = c.turn + nchunks * S;     // (chunk, tree node): children arrived, y's sum
+        c.xt_node = c.cu_node + nchunks * S;  // (chunk, tree node): children arrived, x's sum
+        c.yfin = c.xt_node + nchunks * S;     // tile: chunks whose y is final
         c.xready = c.yfin + N;            // tile: chunks of x published
         c.total = c.xready + N;           // == bs_ctr_ints(nchunks, S, N)
         return c;
@@ -72,8 +73,9 @@ struct BsPersistArgs {
     double* x;
     int64_t psx;
     double* acc;         // [limb][chunk][slice][lane] running sums of the updates
-    double* xt_part;     // [limb][chunk][slice][lane] partial sums of x = U^{-1} y
-    int64_t part_ps;     // plane stride of acc and xt_part
+    double* tree_cu;     // [limb][chunk][node][lane] tree of the sum of a chunk's running sums
+    double* tree_xt;     // [limb][chunk][node][lane] tree of the slices' parts of x = U^{-1} y
+    int64_t part_ps;     // plane stride of acc (the trees: twice that)
     unsigned int* ctr;
     int64_t n;
     int t, N, nchunks, S, KS, ncrit;
@@ -173,11 +175,36 @@ DEV_INLINE bool xt_slice_needed(int cl, int s, int tt) {
     return s * kBsSlice < tt && s * kBsSlice + kBsSlice - 1 >= 32 * cl;
 }
 
-// acc[c][s] := (first ? 0 : acc[c][s]) + v
+// acc[c][s] := (first ? 0 : acc[c][s]) + v; returns the new value
 template <int P>
-DEV_INLINE void acc_add(double* acc, int64_t ps, int64_t off, bool first, const md<P>& v) {
+DEV_INLINE md<P> acc_add(double* acc, int64_t ps, int64_t off, bool first, const md<P>& v) {
     const md<P> r = first ? v : md_add<P>(ld_md_cg<P>(acc, ps, off), v);
     st_md<P>(acc, ps, off, r);
+    return r;
+}
+
+// Sum of the S slice values of one chunk as a binary tree (S a power of two;
+// heap numbering, leaves S .. 2S-1, root 1): a task stores its leaf and
+// climbs; at each node the first of the two children to arrive stops and
+// the second adds left + right (a fixed order whatever the arrival order)
+// and climbs on.  Returns true, with the total in v, to the task that
+// completes the root.  log2(S) dependent additions instead of S - 1.
+template <int P>
+DEV_INLINE bool tree_up(double* tree, int64_t tps, unsigned int* node_cnt, int64_t c, int S, int s, md<P>& v) {
+    const int lane = threadIdx.x & 31;
+    int node = S + s;
+    const int64_t base = c * 2 * S;
+    st_md<P>(tree, tps, (base + node) * 32 + lane, v);
+    while (node > 1) {
+        const int parent = node >> 1;
+        const unsigned old = warp_publish(node_cnt + c * S + parent);
+        if (old == 0) return false;
+        const md<P> other = ld_md_cg<P>(tree, tps, (base + (node ^ 1)) * 32 + lane);
+        v = (node & 1) ? md_add<P>(other, v) : md_add<P>(v, other);
+        node = parent;
+        if (node > 1) st_md<P>(tree, tps, (base + node) * 32 + lane, v);
+    }
+    return true;
 }
 
 template <int P>
@@ -248,21 +275,22 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
                 // after the bulk tiles N-1 .. i+1 of this slice
                 const int nb = N - 1 - i;
                 if (!warp_wait_ge(ctr + C.turn + c * S + s, (unsigned)nb, a.hdr)) return;
-                acc_add<P>(a.acc, pps, (c * S + s) * 32 + lane, nb == 0, part);
-                const unsigned old = warp_publish(ctr + C.cu_cnt + c);
-                if (old != (unsigned)(S - 1)) continue;
-                // last slice of chunk c: y_c - acc[c][0] - ... - acc[c][S-1]
-                md<P> y = ld_md_cg<P>(a.yb, n, r);
-                for (int s2 = 0; s2 < S; ++s2) y = md_sub<P>(y, ld_md_cg<P>(a.acc, pps, (c * S + s2) * 32 + lane));
-                st_md<P>(a.yb, n, r, y);
+                md<P> v = acc_add<P>(a.acc, pps, (c * S + s) * 32 + lane, nb == 0, part);
+                // the chunk's S running sums meet in a tree; the task that
+                // completes it forms y_c - (acc[c][0] + ... + acc[c][S-1])
+                if (!tree_up<P>(a.tree_cu, 2 * pps, ctr + C.cu_node, c, S, s, v)) continue;
+                st_md<P>(a.yb, n, r, md_sub<P>(ld_md_cg<P>(a.yb, n, r), v));
                 warp_publish(ctr + C.yfin + j);
             } else {
                 // x_j = U_j^{-1} y_j: output chunk cl of tile j, slice s of its columns
                 const int j = N - 1 - phase / 2;
                 const int tt = tile_width(n, t, j);
                 const int cl = k / S, s = k % S;
-                if (cl * 32 >= tt || !xt_slice_needed(cl, s, tt)) continue;
-                if (j < N - 1 && !warp_wait_ge(ctr + C.yfin + j, (unsigned)tc, a.hdr)) return;
+                if (cl * 32 >= tt) continue;
+                // slices wholly left of the chunk's diagonal, or beyond a
+                // ragged tile, contribute zero but still enter the tree
+                const bool needed = xt_slice_needed(cl, s, tt);
+                if (needed && j < N - 1 && !warp_wait_ge(ctr + C.yfin + j, (unsigned)tc, a.hdr)) return;
                 const int rl = cl * 32 + lane;  // row within the tile
                 const bool rv = rl < tt;
                 const double* Dj = a.D + (int64_t)j * t * t;
@@ -270,7 +298,7 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
                 double bins[P];
 #pragma unroll
                 for (int l = 0; l < P; ++l) bins[l] = 0.0;
-                const int k0 = s * kBsSlice, k1 = (k0 + kBsSlice) < tt ? (k0 + kBsSlice) : tt;
+                const int k0 = s * kBsSlice, k1 = needed ? ((k0 + kBsSlice) < tt ? (k0 + kBsSlice) : tt) : k0;
                 for (int kk = k0; kk < k1; ++kk) {
                     md<P> dv, yv;
                     const bool in = rv && kk >= rl;  // U^{-1} is upper triangular
@@ -282,20 +310,8 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
                     md_fma_bins<P>(bins, dv, yv);
                 }
                 const int64_t c = (int64_t)j * tc + cl;
-                st_md<P>(a.xt_part, pps, (c * S + s) * 32 + lane, md_from_bins<P>(bins));
-                const unsigned old = warp_publish(ctr + C.xt_cnt + c);
-                int need = 0;
-                for (int s2 = 0; s2 < S; ++s2) need += xt_slice_needed(cl, s2, tt) ? 1 : 0;
-                if (old != (unsigned)(need - 1)) continue;
-                // last slice: x = the slices' sum in slice order
-                md<P> xs = md_zero<P>();
-                bool first = true;
-                for (int s2 = 0; s2 < S; ++s2) {
-                    if (!xt_slice_needed(cl, s2, tt)) continue;
-                    const md<P> v = ld_md_cg<P>(a.xt_part, pps, (c * S + s2) * 32 + lane);
-                    xs = first ? v : md_add<P>(xs, v);
-                    first = false;
-                }
+                md<P> xs = md_from_bins<P>(bins);
+                if (!tree_up<P>(a.tree_xt, 2 * pps, ctr + C.xt_node, c, S, s, xs)) continue;
                 if (rv) st_md<P>(a.x, a.psx, (int64_t)j * t + rl, xs);
                 warp_publish(ctr + C.xready + j);
             }

@@ -592,7 +592,8 @@ int bs_solve_persist(int64_t n, const double* R, int64_t ldr, int64_t psr, const
     a.x = x;
     a.psx = psx;
     a.acc = reinterpret_cast<double*>(ws + L.acc);
-    a.xt_part = reinterpret_cast<double*>(ws + L.xt_part);
+    a.tree_cu = reinterpret_cast<double*>(ws + L.tree_cu);
+    a.tree_xt = reinterpret_cast<double*>(ws + L.tree_xt);
     a.part_ps = L.part_ps;
     a.ctr = ctr;
     a.n = n;

@@ -40,17 +40,17 @@ constexpr int64_t kBsPartCap = 4096;
 struct BsLayout {
     size_t D, b, part;
     // persistent schedule of step 2 (tiles that are multiples of 32 wide):
-    // the per-(chunk, slice) running sums, the slice partial sums of
-    // x = U^{-1} y and the counters
-    size_t acc, xt_part, ctr;
-    int64_t part_ps;  // doubles per plane of acc / xt_part
+    // the per-(chunk, slice) running sums, the two trees of partial sums of
+    // the chain x_i -> x_{i-1} and the counters
+    size_t acc, tree_cu, tree_xt, ctr;
+    int64_t part_ps;  // doubles per plane of acc; the trees hold twice as many
 };
 
 // Persistent back substitution: columns per slice of its products, and the
 // unsigned-int counters it needs (see csrc/bs_persist.cuh).
 constexpr int kBsSliceCols = 8;
 inline int64_t bs_ctr_ints(int64_t nchunks, int64_t S, int64_t N) {
-    return 96 + 2 * 1024 + nchunks * S + 2 * nchunks + 2 * N;
+    return 96 + 2 * 1024 + 3 * nchunks * S + 2 * N;
 }
 
 // Process-wide schedule of the back substitution's step 2 (MDLS_BS_*; set by
@@ -114,13 +114,14 @@ inline BsLayout bs_layout_at(Bump& B, int P, int64_t n, int t) {
     L.D = B.take(d * (size_t)N * t * t);
     L.b = B.take(d * (size_t)n);
     L.part = B.take(d * (size_t)kBsPartCap);
-    L.acc = L.xt_part = L.ctr = 0;
+    L.acc = L.tree_cu = L.tree_xt = L.ctr = 0;
     L.part_ps = 0;
     if (t % 32 == 0) {
         const int64_t nchunks = (n + 31) / 32, S = t / kBsSliceCols;
         L.part_ps = nchunks * S * 32;
         L.acc = B.take(d * (size_t)L.part_ps);
-        L.xt_part = B.take(d * (size_t)L.part_ps);
+        L.tree_cu = B.take(2 * d * (size_t)L.part_ps);
+        L.tree_xt = B.take(2 * d * (size_t)L.part_ps);
         L.ctr = B.take(4 * (size_t)bs_ctr_ints(nchunks, S, N));
     }
     return L;

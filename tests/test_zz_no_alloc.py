@@ -84,7 +84,7 @@ def test_noalloc_size_limits_quoted_in_the_header():
     the fixed scratch, and the next size up does not."""
     mdls, _ = _entry()
     limit = 16 << 20
-    for p, n in ((2, 6400), (4, 3200), (8, 1536)):
+    for p, n in ((2, 4960), (4, 2432), (8, 1152)):
         assert mdls.mdls_backsub_workspace(p, n, 128) <= limit
         assert mdls.mdls_backsub_workspace(p, n + 32, 128) > limit
 
