@@ -391,6 +391,39 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
             return MDLS_ERR_CUDA;
         return MDLS_OK;
     };
+    // 2. WY form of tile k: G = Y^T Y, T from G and the betas, W = -Y T.
+    //    With look-ahead it runs on the side stream right after tile k's
+    //    panel (its own split-K buffer; W alternates between two slots when
+    //    only the current tile's W is kept).
+    auto wy_w = [&](int64_t k) -> double* {
+        const int64_t j0 = k * t;
+        return (want_q || keep_w) ? (Wb + j0 * ldw + j0) : (Wb + (k & 1) * (int64_t)t * ldw);
+    };
+    auto wy = [&](int64_t k, cudaStream_t s, const SplitBuf& sbk) -> int {
+        const int64_t j0 = k * t;
+        const int w = (int)((n - j0) < t ? (n - j0) : t);
+        const int64_t r = m - j0;
+        const double* Yp = A + j0 * lda + j0;
+        ViewTrap Y{Yp, lda, psa};
+        ViewTrapT Yt{Yp, lda, psa};
+        int rc = launch_gemm<P>(ST_W, s, sbk, w, w, r, Yt, Y, Dense{G, t, tt2}, false, false, true);
+        if (rc) return rc;
+        {
+            const int L = w < kTriLeaf ? w : kTriLeaf;
+            StageScope sc(ST_W, s);
+            // one warp (two rows) per block: the leaves spread over w/2 SMs
+            wy_t_leaf_kernel<P><<<(unsigned)((w + 1) / 2), 32, 0, s>>>(G, t, tt2, beta, t, w, L, T, t, tt2);
+            MDLS_LAUNCH_CHECK();
+            rc = tri_levels<P>(ST_W, s, T, t, tt2, 0, G, t, tt2, 0, w, w, 1, L);
+            if (rc) return rc;
+        }
+        return launch_gemm<P>(ST_W, s, sbk, r, w, w, Y, ViewUpper{T, t, tt2}, Dense{wy_w(k), ldw, psw}, true,
+                              false);
+    };
+    // WY products on the side stream only in plain arithmetic (the split
+    // mode's digit buffers are shared by all products)
+    const SplitBuf sb_side{reinterpret_cast<double*>(ws + L.split_side), L.split_side_cap, nullptr, false};
+    const bool wy_side = (L.tc_as_cap == 0);
     // look-ahead only for the one-problem path outside graph capture
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     LookAhead* la = nullptr;
@@ -398,6 +431,7 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
         look_ahead().ok)
         la = &look_ahead();
     bool panel_ahead = false;  // tile k's panel was launched on the side stream
+    bool wy_ahead = false;     // and its WY form after it
     // every return joins the side stream back into st
     struct Join {
         LookAhead* la;
@@ -412,33 +446,25 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
         const int64_t j0 = k * t;
         const int w = (int)((n - j0) < t ? (n - j0) : t);
         const int64_t r = m - j0;
+        const bool have_wy = wy_ahead;
         if (panel_ahead) {
             if (cudaStreamWaitEvent(st, la->done, 0) != cudaSuccess) return MDLS_ERR_CUDA;
             panel_ahead = false;
+            wy_ahead = false;
         } else {
             const int prc = panel(k, st);
             if (prc) return prc;
         }
         const int64_t nc = n + nextra - (j0 + w);  // trailing columns incl. right-hand sides
         if (nc <= 0 && !want_q && !keep_w) continue;
-        // 2. WY form: G = Y^T Y, T from G and the betas, W = -Y T
-        const double* Yp = A + j0 * lda + j0;
-        ViewTrap Y{Yp, lda, psa};
-        ViewTrapT Yt{Yp, lda, psa};
-        int rc = launch_gemm<P>(ST_W, st, sb, w, w, r, Yt, Y, Dense{G, t, tt2}, false, false, true);
-        if (rc) return rc;
-        {
-            const int L = w < kTriLeaf ? w : kTriLeaf;
-            StageScope sc(ST_W, st);
-            // one warp (two rows) per block: the leaves spread over w/2 SMs
-            wy_t_leaf_kernel<P><<<(unsigned)((w + 1) / 2), 32, 0, st>>>(G, t, tt2, beta, t, w, L, T, t, tt2);
-            MDLS_LAUNCH_CHECK();
-            rc = tri_levels<P>(ST_W, st, T, t, tt2, 0, G, t, tt2, 0, w, w, 1, L);
+        int rc = MDLS_OK;
+        if (!have_wy) {
+            rc = wy(k, st, sb);
             if (rc) return rc;
         }
-        double* Wk = (want_q || keep_w) ? (Wb + j0 * ldw + j0) : Wb;
-        rc = launch_gemm<P>(ST_W, st, sb, r, w, w, Y, ViewUpper{T, t, tt2}, Dense{Wk, ldw, psw}, true, false);
-        if (rc) return rc;
+        const double* Yp = A + j0 * lda + j0;
+        ViewTrap Y{Yp, lda, psa};
+        double* Wk = wy_w(k);
         // 3. trailing update C := C + Y (W^T C); with look-ahead first the
         //    next tile's wn columns, then that tile's panel on the side
         //    stream, then the other columns here
@@ -458,8 +484,14 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
                     return MDLS_ERR_CUDA;
                 const int prc = panel(k + 1, la->hi);
                 if (prc) return prc;
-                if (cudaEventRecord(la->done, la->hi) != cudaSuccess) return MDLS_ERR_CUDA;
                 panel_ahead = true;
+                const int64_t nc1 = n + nextra - (j0 + w + wn);
+                if (wy_side && (nc1 > 0 || want_q || keep_w)) {
+                    const int wrc = wy(k + 1, la->hi, sb_side);
+                    if (wrc) return wrc;
+                    wy_ahead = true;
+                }
+                if (cudaEventRecord(la->done, la->hi) != cudaSuccess) return MDLS_ERR_CUDA;
                 double* Cq = Cp + nfirst * lda;
                 double* Xq = X + nfirst * t;
                 rc = launch_gemm<P>(ST_TRAIL, st, sb, w, nc - nfirst, r, ViewDenseT{Wk, ldw, psw},

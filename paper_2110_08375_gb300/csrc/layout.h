@@ -26,8 +26,8 @@ constexpr int fx_digits(int P) { return (53 * P + 64 + 23) / 24; }
 constexpr int fx_meta_ints(int P) { return 4 + 2 * (fx_digits(P) + 1); }
 
 struct QrLayout {
-    size_t flags, flag_bytes, beta, fxF, fxmeta, G, T, X, W, split;
-    int64_t xcols, wcols, split_cap;
+    size_t flags, flag_bytes, beta, fxF, fxmeta, G, T, X, W, split, split_side;
+    int64_t xcols, wcols, split_cap, split_side_cap;
     // tensor-core digit slices (split mode; caps 0 otherwise)
     size_t tc_as, tc_bs, tc_ea, tc_fb, tc_as_cap, tc_bs_cap;
     int64_t tc_sc_cap;
@@ -78,7 +78,9 @@ inline QrLayout qr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool w
     L.xcols = n + nextra;
     if (want_q && m > L.xcols) L.xcols = m;
     L.X = B.take(d * t * (size_t)L.xcols);
-    L.wcols = (want_q || keep_w) ? n : t;
+    // every tile's W, or two tiles' W: the next tile's W is formed beside
+    // the current tile's trailing update, which still reads its own
+    L.wcols = (want_q || keep_w) ? n : 2 * (int64_t)t;
     L.W = B.take(d * (size_t)m * (size_t)L.wcols);
     // split-K partial sums, md values per plane: room for 8 partial products
     // of a tile's W^T C (t x xcols), so that a product of one to two waves
@@ -86,6 +88,9 @@ inline QrLayout qr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool w
     L.split_cap = 16 * (int64_t)t * t;
     if (8 * (int64_t)t * L.xcols > L.split_cap) L.split_cap = 8 * (int64_t)t * L.xcols;
     L.split = B.take(d * (size_t)L.split_cap);
+    // split-K partial sums of the next tile's G = Y^T Y on the side stream
+    L.split_side_cap = 16 * (int64_t)t * t;
+    L.split_side = B.take(d * (size_t)L.split_side_cap);
     L.tc_as = L.tc_bs = L.tc_ea = L.tc_fb = 0;
     L.tc_as_cap = L.tc_bs_cap = 0;
     L.tc_sc_cap = 0;
