@@ -193,9 +193,14 @@ int tri_levels(int stage, cudaStream_t st, double* X, int64_t ldx, int64_t psx, 
                int64_t ntiles, int L) {
     StageScope sc(stage, st);
     for (int s = L; s < t; s *= 2) {
-        int KS = 1;  // k groups of at most 8 (16 for s = 128)
-        while (KS * 8 < s && KS < 8) KS *= 2;
         const int nbi = (s + 7) / 8, nbj = (s + 3) / 4;
+        // k groups of at least 8 values of k (16 for s = 128) when the level
+        // has few blocks; of at least 32 when the blocks of all tiles already
+        // hold eight warps per SM
+        const int64_t blocks = (int64_t)nbi * nbj * ((t + 2 * s - 1) / (2 * s)) * ntiles;
+        const int kmin = blocks >= 8 * (int64_t)sm_count() ? 32 : 8;
+        int KS = 1;
+        while (KS * kmin < s && KS < 8) KS *= 2;
         dim3 grid((unsigned)(nbi * nbj), (unsigned)((t + 2 * s - 1) / (2 * s)), (unsigned)ntiles);
         const size_t smem = (size_t)KS * 32 * sizeof(md<P>);
         tri_level_kernel<P, 0><<<grid, 32 * KS, smem, st>>>(X, ldx, psx, xtile, M, ldm, psm, mtile, n, t, s);

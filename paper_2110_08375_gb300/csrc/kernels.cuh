@@ -326,12 +326,14 @@ __global__ void split_reduce_kernel(int64_t M, int64_t N, int S, const double* p
 constexpr int kTriLeaf = 16;
 
 // Leaves of the tile inversion: column c of the inverse of an L x L diagonal
-// block (leaf) of tile `tile` solves U v = e_c by back substitution,
-// v_c = 1/U_cc and v_l = -(sum_{q=l+1}^{c} U_lq v_q) / U_ll for l < c.  Two
-// columns per warp, one per half; lane h of a half holds v_h and the
-// reciprocal of U_hh (computed once, in parallel).  A zero pivot records
-// MDLS_ERR_SINGULAR (its reciprocal reads as zero).  Column c of tile `tile`
-// goes to D + tile * dtile + c * dld (rows of its leaf only).
+// block (leaf) of tile `tile` solves U v = e_c by back substitution, column
+// by column: with s = e_c, for l = c down to 0, v_l = s_l / U_ll, then
+// s_h -= U_hl v_l for every h < l.  Two columns per warp, one per half; lane
+// h of a half holds s_h, v_h and the reciprocal of U_hh (computed once, in
+// parallel), so a step is one product, one broadcast and one fused
+// multiply-subtract per lane: no reductions on the serial chain.  A zero
+// pivot records MDLS_ERR_SINGULAR (its reciprocal reads as zero).  Column c
+// of tile `tile` goes to D + tile * dtile + c * dld (rows of its leaf only).
 template <int P>
 __global__ void tri_leaf_inv_kernel(const double* U, int64_t ld, int64_t ps, int64_t n, int t, int L,
                                     int64_t ntiles, double* D, int64_t dld, int64_t dps, int64_t dtile,
@@ -357,15 +359,13 @@ __global__ void tri_leaf_inv_kernel(const double* U, int64_t ld, int64_t ps, int
         if (d.v[0] == 0.0) set_status(&hdr->status, MDLS_ERR_SINGULAR);
         else r = md_div<P>(md_one<P>(), d);
     }
-    md<P> v = (valid && h == k) ? r : md_zero<P>();
+    md<P> acc = (valid && h == k) ? md_one<P>() : md_zero<P>();  // s_h
+    md<P> v = md_zero<P>();
     const int kw = ((c0 + 1) < tt ? (c0 + 1) : c0) - leaf0;  // largest column of the warp
-    for (int l = kw - 1; l >= 0; --l) {
-        const bool act = valid && l < k;
-        const bool in = act && h > l && h <= k;
-        const md<P> u = in ? ld_md<P>(Ul, ps, (int64_t)h * ld + l) : md_zero<P>();
-        const md<P> sum = half_sum<P>(md_mul<P>(u, v));
-        const md<P> vl = md_neg<P>(md_mul<P>(sum, half_shfl<P>(r, l)));
-        v = md_select<P>(act && h == l, vl, v);
+    for (int l = kw; l >= 0; --l) {
+        const md<P> vl = half_shfl<P>(md_mul<P>(acc, r), l);  // v_l, from lane l of the half
+        v = md_select<P>(valid && h == l && l <= k, vl, v);
+        if (valid && h < l && l <= k) acc = md_fms<P>(acc, ld_md<P>(Ul, ps, (int64_t)l * ld + h), vl);
     }
     if (valid && h <= k) st_md<P>(D + tile * dtile + (int64_t)c * dld, dps, leaf0 + h, v);
 }
@@ -408,8 +408,9 @@ __global__ void wy_t_leaf_kernel(const double* G, int64_t ldg, int64_t psg, cons
 //   STEP 1: X12 = -X1 Z (X1 upper triangular: k >= i) into X[a+i, a+s+j].
 // An 8 x 4 output block per warp (lanes along i: coalesced reads of M12 and
 // X1); the k range is split over blockDim.x / 32 (at most 8) warps whose
-// partial sums meet in a fixed tree.  Small blocks spread a level over most
-// SMs: each SM's shared FP64 unit, not the number of outputs, sets the pace.
+// partial sums meet in a fixed tree.  Small blocks spread a level of one tile
+// over most SMs: each SM's shared FP64 unit, not the number of outputs, sets
+// the pace; with many tiles the k ranges are longer and the tree shorter.
 template <int P, int STEP>
 __global__ void __launch_bounds__(256) tri_level_kernel(double* X, int64_t ldx, int64_t psx, int64_t xtile, const double* M,
                                  int64_t ldm, int64_t psm, int64_t mtile, int64_t n, int t, int s) {
@@ -431,19 +432,23 @@ __global__ void __launch_bounds__(256) tri_level_kernel(double* X, int64_t ldx, 
 #pragma unroll
     for (int l = 0; l < P; ++l) bins[l] = 0.0;
     if (out) {
-        const int kc = (s + KS - 1) / KS;  // at most 16
+        const int kc = (s + KS - 1) / KS;
         int kb = kz * kc, ke = kb + kc;
         if (STEP == 0) {
             ke = ke < j + 1 ? ke : j + 1;
-            for (int k = kb; k < ke; ++k)
+            for (int k = kb; k < ke; ++k) {
                 md_fma_bins<P>(bins, ld_md<P>(Mb, psm, (a + s + k) * ldm + a + i),
                                ld_md<P>(Xb, psx, (a + s + j) * ldx + a + s + k));
+                if (((k - kb) & 15) == 15) md_bins_renorm<P>(bins);
+            }
         } else {
             kb = kb > i ? kb : i;
             ke = ke < s ? ke : s;
-            for (int k = kb; k < ke; ++k)
+            for (int k = kb; k < ke; ++k) {
                 md_fma_bins<P>(bins, ld_md<P>(Xb, psx, (a + k) * ldx + a + i),
                                ld_md<P>(Xb, psx, (a + k) * ldx + a + s + j));
+                if (((k - kb) & 15) == 15) md_bins_renorm<P>(bins);
+            }
         }
     }
     red[kz * 32 + lane] = md_from_bins<P>(bins);
