@@ -15,10 +15,11 @@
 //    columns; every (chunk c, slice s) keeps a running sum acc[c][s] of its
 //    terms sum_k R(c, k) x_k over the tiles met so far;
 //  * bulk tasks (c, i, s) -- chunks at least two tiles above tile i -- come
-//    from one queue in order of i, then c downwards, then s: a task computes
-//    its kBsSlice-column product as soon as x_i is published and adds it to
-//    acc[c][s] once the tiles N..i+1 are in (the turn counter of (c, s)), so
-//    every sum is formed in the same order in every run (deterministic);
+//    from one queue in order of i, then c downwards, then s: once x_i is
+//    published and the tiles N..i+1 are in acc[c][s] (the turn counter of
+//    (c, s)), a task continues that running sum with its kBsSlice-column
+//    product, so every sum is formed in the same order in every run
+//    (deterministic);
 //  * the critical chain x_i -> x_{i-1} runs on a few reserved SMs (the other
 //    blocks on them stay idle, so each critical warp has an FP64 pipe of its
 //    own): the slices of tile i-1's rows times x_i join their running sums,
@@ -41,7 +42,7 @@ namespace mdls {
 
 constexpr int kBsSlice = kBsSliceCols;  // columns per slice
 constexpr int kBsCritSms = 16;          // SMs reserved for the critical chain
-constexpr int kBsBlocksPerSm = 3;       // 128-thread blocks per SM: three warps per sub-partition
+constexpr int kBsBlocksPerSm = 4;       // 128-thread blocks per SM: four warps per sub-partition
 constexpr int kBsMaxSm = 1024;          // slots of the per-SM role claim
 
 // Counters (unsigned ints, zeroed by the host before the launch).
@@ -157,6 +158,29 @@ DEV_INLINE md<P> rows_times_x(const double* A, int64_t lda, int64_t psa, int64_t
         if ((++cnt & 15) == 0) md_bins_renorm<P>(bins);
     }
     return md_from_bins<P>(bins);
+}
+
+// acc[c][s] := (first ? 0 : acc[c][s]) + sum_{k in [k0, k1)} A(r, k) x_k: the
+// running sum is the addend of the product's bins, so a bulk task costs one
+// renormalisation and no md addition of its own.
+template <int P>
+DEV_INLINE void acc_rows_times_x(double* acc, int64_t ps, int64_t off, bool first, const double* A, int64_t lda,
+                                 int64_t psa, int64_t r, int64_t k0, int64_t k1, const double* x, int64_t psx) {
+    double bins[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) bins[l] = first ? 0.0 : __ldcg(acc + l * ps + off);
+    int cnt = 0;
+    for (int64_t k = k0; k < k1; ++k) {
+        md<P> a, xv;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            a.v[l] = A[l * psa + k * lda + r];
+            xv.v[l] = __ldcg(x + l * psx + k);
+        }
+        md_fma_bins<P>(bins, a, xv);
+        if ((++cnt & 15) == 0) md_bins_renorm<P>(bins);
+    }
+    st_md<P>(acc, ps, off, md_from_bins<P>(bins));
 }
 
 // Columns [k0, k1) of slice s of tile i (empty beyond a ragged last tile).
@@ -340,11 +364,13 @@ __global__ void __launch_bounds__(128) bs_persist_kernel(BsPersistArgs a) {
         const int64_t r = c * 32 + lane;
         int64_t k0, k1;
         slice_cols(n, t, i, s, k0, k1);
-        const md<P> part = rows_times_x<P>(a.R, a.ldr, a.psr, r, k0, k1, a.x, a.psx);
-        // add in the slice's fixed order: tiles N-1, N-2, ..., i+1 before i
+        // in the slice's fixed order: tiles N-1, N-2, ..., i+1 before i (the
+        // queue hands out a slice's tiles a whole step apart, so the turn is
+        // almost always there)
         const int nb = N - 1 - i;
         if (!warp_wait_ge(ctr + C.turn + c * S + s, (unsigned)nb, a.hdr)) return;
-        acc_add<P>(a.acc, pps, (c * S + s) * 32 + lane, nb == 0, part);
+        acc_rows_times_x<P>(a.acc, pps, (c * S + s) * 32 + lane, nb == 0, a.R, a.ldr, a.psr, r, k0, k1, a.x,
+                            a.psx);
         warp_publish(ctr + C.turn + c * S + s);
     }
 }
