@@ -320,6 +320,17 @@ def run_gpu(args):
                 "op": "one FP64 instruction (DADD, DMUL or DFMA each occupy one FP64 pipe slot)",
                 "peak_source": "FP64 pipe issue rate 2/clk/SM (ncu peak_sustained) x 152 SMs x 2.07 GHz",
                 "dominant_stage": dominant}
+    # the same FP64 pipe over the whole step: the next tile's WY products run
+    # beside the trailing update, so the stage's own events include time the
+    # two share; here the FP64 instructions of both kinds of products over the
+    # step's wall time
+    step_ops = sum((opcount.trailing_md_fmas(n, n, t, extra_cols=1) + opcount.wy_md_fmas(n, n, t, extra_cols=1))
+                   * opcount.gemm_fma_cost(p) for p in precs) * args.steps
+    step_rate = step_ops / (total_ms / 1e3) / 1e12
+    roofline["whole_step"] = {"achieved": step_rate, "frac": step_rate / FP64_PEAK_TOPS,
+                              "work": "FP64 instructions of the trailing-update and WY products of every "
+                                      "precision, over the step's wall time (panels, T and back "
+                                      "substitution earn nothing)"}
 
     checks = {}
     for p in precs:

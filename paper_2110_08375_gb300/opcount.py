@@ -188,3 +188,17 @@ def trailing_md_fmas(m: int, n: int, t: int, extra_cols: int = 0) -> int:
         if nc > 0:
             total += 2 * w * nc * r
     return total
+
+
+def wy_md_fmas(m: int, n: int, t: int, extra_cols: int = 0) -> int:
+    """md FMAs of the WY form's two products over all tiles that have a
+    trailing update: G = Y^T Y (upper triangle, w (w+1)/2 outputs of r
+    terms) and W = -Y T (T upper triangular: r x w outputs, j + 1 terms for
+    column j)."""
+    total = 0
+    for j0 in range(0, n, t):
+        w = min(t, n - j0)
+        r = m - j0
+        if n + extra_cols - (j0 + w) > 0:
+            total += 2 * (w * (w + 1) // 2) * r
+    return total

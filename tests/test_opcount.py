@@ -87,3 +87,21 @@ def test_two_sum_form_per_bin():
     # once per 16 steps
     expect = (55 * 1 + 85 * 3) + 28 * 2 + (8 + 7 + 49) + 13 * 3 / 16
     assert abs(opcount.gemm_fma_cost(8) - expect) < 1e-9
+
+
+@pytest.mark.parametrize("m,n,t", [(10, 7, 3), (16, 16, 4), (9, 9, 9)])
+def test_product_counts_by_enumeration(m, n, t):
+    # one md FMA per (output, term) of X = W^T C, C += Y X, G = Y^T Y (upper
+    # triangle) and W = -Y T (T upper triangular), enumerated term by term
+    trail = wy = 0
+    for j0 in range(0, n, t):
+        w, r = min(t, n - j0), m - j0
+        nc = n + 1 - (j0 + w)
+        if nc <= 0:
+            continue
+        trail += sum(1 for _i in range(w) for _j in range(nc) for _k in range(r))
+        trail += sum(1 for _i in range(r) for _j in range(nc) for _k in range(w))
+        wy += sum(1 for i in range(w) for j in range(i, w) for _k in range(r))
+        wy += sum(1 for _i in range(r) for j in range(w) for _k in range(j + 1))
+    assert opcount.trailing_md_fmas(m, n, t, extra_cols=1) == trail
+    assert opcount.wy_md_fmas(m, n, t, extra_cols=1) == wy
