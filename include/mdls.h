@@ -143,6 +143,30 @@ size_t mdls_backsub_workspace(int prec, int64_t n, int tile);
 int mdls_set_backsub_schedule(int schedule);
 
 /*
+ * mdls_set_split_engine -- which tensor-core kernel evaluates the digit
+ * products of MDLS_MODE_SPLIT (and of the double double factorisation of
+ * MDLS_MODE_REFINE), for every later call of this process.  Both compute the
+ * same exact sums of digit products (the error-free splitting of the WY
+ * products, Section 3's trailing update and Q accumulation):
+ *   MDLS_SPLIT_ENGINE_TCGEN05: fifth-generation tensor cores (tcgen05.mma,
+ *     accumulators in tensor memory, operands staged by bulk copies), one
+ *     128-row tile per block, K split over blocks when the tiles alone leave
+ *     SMs idle (the blocks' exact partial products are then rounded to prec
+ *     limbs and added in a fixed order);
+ *   MDLS_SPLIT_ENGINE_MMA_SYNC: warp-level mma.sync m16n8k16, 16 x 8 tiles,
+ *     K never split;
+ *   MDLS_SPLIT_ENGINE_AUTO (default): tcgen05 for products of at least 64
+ *     rows and 16 columns of single problems, mma.sync for the rest and for
+ *     every product of mdls_lstsq_batched / mdls_batched_*.
+ * Without a K split the two give bit-identical products.  Not meant to change
+ * while calls are in flight.  Returns MDLS_OK or MDLS_ERR_ARG.
+ */
+#define MDLS_SPLIT_ENGINE_AUTO 0
+#define MDLS_SPLIT_ENGINE_MMA_SYNC 1
+#define MDLS_SPLIT_ENGINE_TCGEN05 2
+int mdls_set_split_engine(int engine);
+
+/*
  * mdls_backsub_noalloc -- the same back substitution as mdls_backsub, for
  * callers that cannot allocate device memory when they call: a plugin inside
  * a host framework that owns all device memory through its own allocator, a

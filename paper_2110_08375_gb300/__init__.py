@@ -92,6 +92,7 @@ def lib() -> C.CDLL:
     L.mdls_vec_op.argtypes = [C.c_int, C.c_int, i64, vp, i64, vp, i64, vp, i64, vp]
     L.mdls_wait_check.argtypes = [vp, sz, C.c_uint64, C.c_int, vp]
     L.mdls_set_backsub_schedule.argtypes = [C.c_int]
+    L.mdls_set_split_engine.argtypes = [C.c_int]
     L.mdls_toeplitz_lstsq_workspace.argtypes = [C.c_int, i64, i64, C.c_int]
     L.mdls_toeplitz_lstsq_workspace.restype = sz
     L.mdls_toeplitz_lstsq.argtypes = [C.c_int, i64, i64, i64, vp, i64, i64, i64, vp, i64, i64, vp, i64, i64,
@@ -345,6 +346,17 @@ def mdls_set_backsub_schedule(schedule: int) -> None:
 
 
 WAIT_CHECK_WORKSPACE = 512
+
+
+SPLIT_ENGINE_AUTO, SPLIT_ENGINE_MMA_SYNC, SPLIT_ENGINE_TCGEN05 = 0, 1, 2
+
+
+def mdls_set_split_engine(engine: int) -> None:
+    """Kernel of the split-mode digit products: tcgen05 (SPLIT_ENGINE_TCGEN05),
+    mma.sync (SPLIT_ENGINE_MMA_SYNC) or chosen by shape (SPLIT_ENGINE_AUTO)."""
+    rc = lib().mdls_set_split_engine(int(engine))
+    if rc != 0:
+        raise MdlsError(rc, "mdls_set_split_engine")
 
 
 def mdls_wait_check(limit_ns: int, publish: bool, ws=None, stream=None):

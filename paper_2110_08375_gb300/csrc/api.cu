@@ -42,6 +42,11 @@ int& mdls::bs_schedule_ref() {
     return s;
 }
 
+int& mdls::split_engine_ref() {
+    static int e = MDLS_SPLIT_ENGINE_AUTO;
+    return e;
+}
+
 static bool prec_ok(int p) { return p == 2 || p == 4 || p == 8; }
 
 static bool ws_ok(const void* ws, size_t have, size_t need) {
@@ -269,6 +274,14 @@ int mdls_set_backsub_schedule(int schedule) {
     if (schedule != MDLS_BS_AUTO && schedule != MDLS_BS_PER_STEP && schedule != MDLS_BS_PERSISTENT)
         return MDLS_ERR_ARG;
     bs_schedule_ref() = schedule;
+    return MDLS_OK;
+}
+
+int mdls_set_split_engine(int engine) {
+    if (engine != MDLS_SPLIT_ENGINE_AUTO && engine != MDLS_SPLIT_ENGINE_MMA_SYNC &&
+        engine != MDLS_SPLIT_ENGINE_TCGEN05)
+        return MDLS_ERR_ARG;
+    split_engine_ref() = engine;
     return MDLS_OK;
 }
 

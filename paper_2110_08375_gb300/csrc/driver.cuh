@@ -5,6 +5,7 @@
 
 #include "kernels.cuh"
 #include "split.cuh"
+#include "split_tc.cuh"
 #include "layout.h"
 #include "panel_fx.cuh"
 #include "bs_persist.cuh"
@@ -61,6 +62,7 @@ struct TcBuf {
     int* fb;
     size_t as_cap, bs_cap;  // bf16 elements
     int64_t sc_cap;         // ints in ea and in fb
+    WsHeader* hdr;          // status word and wait limit of the tcgen05 products
 };
 
 // Scratch for split-K partial sums (cap md values per plane), and the
@@ -74,11 +76,13 @@ struct SplitBuf {
 
 template <int P>
 void split_gemm_setup() {
-    static bool done = false;
-    if (!done) {
+    static bool done[kMaxDev] = {};
+    const int dev = cur_dev();
+    const int d = (dev >= 0 && dev < kMaxDev) ? dev : kMaxDev - 1;
+    if (!done[d]) {
         cudaFuncSetAttribute(split_gemm_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)split_gemm_smem<P>());
-        done = true;
+        done[d] = true;
     }
 }
 
@@ -100,6 +104,83 @@ int launch_split_gemm(int stage, cudaStream_t st, const TcBuf& tc, int64_t M, in
                                                                  neg ? 1 : 0, acc ? 1 : 0);
     MDLS_LAUNCH_CHECK();
     (void)S;
+    return MDLS_OK;
+}
+
+// Which split-product kernel a product uses (mdls_set_split_engine):
+// automatic (tcgen05 for products of at least 64 rows and 16 columns on a
+// whole GPU, mma.sync otherwise), mma.sync only, or tcgen05 wherever the
+// slices fit.
+template <int P>
+bool split_tc_setup() {
+    static bool done[kMaxDev] = {};
+    static bool ok[kMaxDev] = {};
+    const int dev = cur_dev();
+    const int d = (dev >= 0 && dev < kMaxDev) ? dev : kMaxDev - 1;
+    if (!done[d]) {
+        ok[d] = cudaFuncSetAttribute(split_gemm_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)split_tc_smem<P>()) == cudaSuccess;
+        done[d] = true;
+    }
+    return ok[d];
+}
+
+template <int P>
+bool split_tc_eligible(const TcBuf& tc, const SplitBuf& sb, int64_t M, int64_t N, int64_t K) {
+    const int eng = split_engine_ref();
+    if (eng == MDLS_SPLIT_ENGINE_MMA_SYNC || tc.hdr == nullptr) return false;
+    if (eng == MDLS_SPLIT_ENGINE_AUTO && (!sb.whole_gpu || M < 64 || N < 16)) return false;
+    using Cfg = TcCfg<P>;
+    const int64_t Kp = (K + 15) / 16 * 16;
+    const int64_t Mp = (M + kTcRows - 1) / kTcRows * kTcRows, Np = (N + Cfg::NT - 1) / Cfg::NT * Cfg::NT;
+    return (size_t)Cfg::S * Mp * Kp <= tc.as_cap && (size_t)Cfg::SP * Np * Kp <= tc.bs_cap && M <= tc.sc_cap &&
+           N <= tc.sc_cap;
+}
+
+// C = [C] +/- A B through the digit slices on tcgen05 (split_tc.cuh).  When
+// the output tiles alone would leave SMs idle, K is split over grid.y (each
+// block's exact partial product rounded to P limbs into `sb`, added in a
+// fixed order by split_reduce_kernel).
+template <int P, class AV, class BV>
+int launch_split_gemm_tc(int stage, cudaStream_t st, const TcBuf& tc, const SplitBuf& sb, int64_t M, int64_t N,
+                         int64_t K, AV a, BV b, Dense c, bool neg, bool acc) {
+    using Cfg = TcCfg<P>;
+    if (!split_tc_setup<P>()) return MDLS_ERR_CUDA;
+    const int64_t KB16 = (K + 15) / 16;
+    const int64_t Mp = (M + kTcRows - 1) / kTcRows * kTcRows, Np = (N + Cfg::NT - 1) / Cfg::NT * Cfg::NT;
+    StageScope sc(stage, st);
+    split_rows_tc_kernel<P, kTcRows, Cfg::S, AV><<<(unsigned)((Mp * 32 + 255) / 256), 256, 0, st>>>(
+        M, Mp, K, KB16, a, tc.As, tc.ea);
+    MDLS_LAUNCH_CHECK();
+    split_rows_tc_kernel<P, Cfg::NT, Cfg::SP, ViewTranspose<BV>><<<(unsigned)((Np * 32 + 255) / 256), 256, 0, st>>>(
+        N, Np, K, KB16, ViewTranspose<BV>{b}, tc.Bs, tc.fb);
+    MDLS_LAUNCH_CHECK();
+    const int64_t tiles = (Mp / kTcRows) * (Np / Cfg::NT);
+    const int64_t groups = (KB16 + Cfg::DK - 1) / Cfg::DK;
+    int64_t ks = 1;
+    const int64_t sms = sm_count();
+    if (tiles < sms && sb.ptr != nullptr && groups >= 2) {
+        ks = (sms + tiles - 1) / tiles;
+        if (ks > 16) ks = 16;
+        if (ks > groups) ks = groups;
+        while (ks > 1 && ks * M * N > sb.cap) --ks;
+    }
+    int64_t kb_per = (groups + ks - 1) / ks * Cfg::DK;
+    ks = (KB16 + kb_per - 1) / kb_per;
+    dim3 grid((unsigned)tiles, (unsigned)ks);
+    if (ks == 1) {
+        split_gemm_tc_kernel<P><<<grid, kTcThreads, split_tc_smem<P>(), st>>>(
+            M, N, KB16, kb_per, tc.As, tc.Bs, tc.ea, tc.fb, c, neg ? 1 : 0, acc ? 1 : 0, 0, tc.hdr);
+        MDLS_LAUNCH_CHECK();
+        return MDLS_OK;
+    }
+    split_gemm_tc_kernel<P><<<grid, kTcThreads, split_tc_smem<P>(), st>>>(
+        M, N, KB16, kb_per, tc.As, tc.Bs, tc.ea, tc.fb, Dense{sb.ptr, M, sb.cap}, 0, 0, M * N, tc.hdr);
+    MDLS_LAUNCH_CHECK();
+    const int64_t total = M * N;
+    split_reduce_kernel<P><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(M, N, (int)ks, sb.ptr, M, sb.cap, M * N,
+                                                                          c, neg ? 1 : 0, acc ? 1 : 0);
+    MDLS_LAUNCH_CHECK();
     return MDLS_OK;
 }
 
@@ -211,18 +292,22 @@ int tri_levels(int stage, cudaStream_t st, double* X, int64_t ldx, int64_t psx, 
     return MDLS_OK;
 }
 
-// Resident blocks per SM of one md GEMM instance (occupancy query, once).
+// Resident blocks per SM of one md GEMM instance (occupancy query, once per
+// device).
 template <int P, class AV, class BV>
 int gemm_blocks_per_sm() {
-    static const int nb = [] {
+    static int nb[kMaxDev] = {};
+    const int dev = cur_dev();
+    const int d = (dev >= 0 && dev < kMaxDev) ? dev : kMaxDev - 1;
+    if (nb[d] == 0) {
         int v = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_kernel<P, AV, BV>, kGemmTile * gemm_tn<P>(), 0) !=
                 cudaSuccess ||
             v < 1)
             v = 1;
-        return v;
-    }();
-    return nb;
+        nb[d] = v;
+    }
+    return nb[d];
 }
 
 // Launches one md GEMM.  The K range may be split over grid.z (at most 16
@@ -239,6 +324,8 @@ int launch_gemm(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t N, i
                 Dense c, bool neg, bool acc, bool upper_only = false) {
     if (M <= 0 || N <= 0) return MDLS_OK;
     if (sb.tc != nullptr && K > 0) {
+        if (split_tc_eligible<P>(*sb.tc, sb, M, N, K))
+            return launch_split_gemm_tc<P>(stage, st, *sb.tc, sb, M, N, K, a, b, c, neg, acc);
         const int64_t Kp = (K + kSplitTk - 1) / kSplitTk * kSplitTk;
         constexpr int S = SplitCfg<P>::S;
         if ((size_t)S * M * Kp <= sb.tc->as_cap && (size_t)S * N * Kp <= sb.tc->bs_cap &&
@@ -307,13 +394,15 @@ int launch_gemm(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t N, i
 // Largest panel width the column-per-block cooperative panel can hold.
 template <int P>
 int panel_capacity() {
-    static int cap = -1;
-    if (cap < 0) {
+    static int cap[kMaxDev] = {};
+    const int dev = cur_dev();
+    const int d = (dev >= 0 && dev < kMaxDev) ? dev : kMaxDev - 1;
+    if (cap[d] <= 0) {
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fx_panel_kernel<P, fx_panel_threads<P>()>, fx_panel_threads<P>(), 0);
-        cap = sm_count() * per;
+        cap[d] = sm_count() * per;
     }
-    return cap;
+    return cap[d];
 }
 
 // Look-ahead: the next tile's panel runs on a high-priority side stream
@@ -327,17 +416,21 @@ struct LookAhead {
 };
 
 inline LookAhead& look_ahead() {
-    thread_local LookAhead la;
-    thread_local bool tried = false;
-    if (!tried) {
-        tried = true;
+    // per host thread and per device: the side stream and its events belong
+    // to the device that was current when they were created
+    thread_local LookAhead la[kMaxDev];
+    thread_local bool tried[kMaxDev] = {};
+    const int dev = cur_dev();
+    const int d = (dev >= 0 && dev < kMaxDev) ? dev : kMaxDev - 1;
+    if (!tried[d]) {
+        tried[d] = true;
         int least = 0, greatest = 0;
-        la.ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
-                cudaStreamCreateWithPriority(&la.hi, cudaStreamNonBlocking, greatest) == cudaSuccess &&
-                cudaEventCreateWithFlags(&la.ready, cudaEventDisableTiming) == cudaSuccess &&
-                cudaEventCreateWithFlags(&la.done, cudaEventDisableTiming) == cudaSuccess;
+        la[d].ok = dev == d && cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+                   cudaStreamCreateWithPriority(&la[d].hi, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&la[d].ready, cudaEventDisableTiming) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&la[d].done, cudaEventDisableTiming) == cudaSuccess;
     }
-    return la;
+    return la[d];
 }
 
 // Blocked Householder QR (Algorithm 2) of the m x n leading part of the
@@ -363,7 +456,7 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
     if (L.tc_as_cap > 0) {
         tcb = TcBuf{reinterpret_cast<__nv_bfloat16*>(ws + L.tc_as), reinterpret_cast<__nv_bfloat16*>(ws + L.tc_bs),
                     reinterpret_cast<int*>(ws + L.tc_ea), reinterpret_cast<int*>(ws + L.tc_fb),
-                    L.tc_as_cap, L.tc_bs_cap, L.tc_sc_cap};
+                    L.tc_as_cap, L.tc_bs_cap, L.tc_sc_cap, hdr};
     }
     const SplitBuf sb{reinterpret_cast<double*>(ws + L.split), L.split_cap,
                       L.tc_as_cap > 0 ? &tcb : nullptr, !single_block};

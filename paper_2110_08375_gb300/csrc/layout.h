@@ -56,6 +56,7 @@ inline int64_t bs_ctr_ints(int64_t nchunks, int64_t S, int64_t N) {
 // Process-wide schedule of the back substitution's step 2 (MDLS_BS_*; set by
 // mdls_set_backsub_schedule, defined in api.cu).
 int& bs_schedule_ref();
+int& split_engine_ref();
 struct LsLayout {
     QrLayout qr;
     size_t Aw;
@@ -103,6 +104,13 @@ inline QrLayout qr_layout_at(Bump& B, int P, int64_t m, int64_t n, int t, bool w
         if (t > bcols) bcols = t;
         L.tc_as_cap = (size_t)S * (size_t)((t * mp > m * tp) ? t * mp : m * tp);
         L.tc_bs_cap = (size_t)S * (size_t)(bcols * mp);
+        // the tcgen05 products' tiled slices: A rows padded to 128, B rows to
+        // 16, one more B slice (octo double's padding slice)
+        const int64_t m128 = (m + 127) / 128 * 128, t128 = (t + 127) / 128 * 128;
+        const size_t tiled_a = (size_t)S * (size_t)((t128 * mp > m128 * tp) ? t128 * mp : m128 * tp);
+        const size_t tiled_b = (size_t)(S + 1) * (size_t)(round16(bcols) * mp);
+        if (tiled_a > L.tc_as_cap) L.tc_as_cap = tiled_a;
+        if (tiled_b > L.tc_bs_cap) L.tc_bs_cap = tiled_b;
         L.tc_sc_cap = (m > bcols ? m : bcols);
         L.tc_as = B.take(2 * L.tc_as_cap);
         L.tc_bs = B.take(2 * L.tc_bs_cap);

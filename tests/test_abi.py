@@ -129,6 +129,14 @@ def test_backsub_schedule_argument(L):
         assert L.mdls_set_backsub_schedule(s) == 0
 
 
+def test_split_engine_argument(L):
+    import paper_2110_08375_gb300 as pkg
+    assert L.mdls_set_split_engine(3) == -1
+    assert L.mdls_set_split_engine(-1) == -1
+    for e in (pkg.SPLIT_ENGINE_MMA_SYNC, pkg.SPLIT_ENGINE_TCGEN05, pkg.SPLIT_ENGINE_AUTO):
+        assert L.mdls_set_split_engine(e) == 0
+
+
 def test_toeplitz_argument_errors(L):
     vp = C.c_void_p
     fake = vp(1 << 20)
