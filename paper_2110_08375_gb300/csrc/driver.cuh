@@ -149,21 +149,35 @@ int launch_split_gemm_tc(int stage, cudaStream_t st, const TcBuf& tc, const Spli
     const int64_t KB16 = (K + 15) / 16;
     const int64_t Mp = (M + kTcRows - 1) / kTcRows * kTcRows, Np = (N + Cfg::NT - 1) / Cfg::NT * Cfg::NT;
     StageScope sc(stage, st);
-    split_rows_tc_kernel<P, kTcRows, Cfg::S, AV><<<(unsigned)((Mp * 32 + 255) / 256), 256, 0, st>>>(
+    const unsigned kch = (unsigned)((KB16 * 16 + kTcConvK - 1) / kTcConvK);
+    split_scale_kernel<AV><<<(unsigned)((M * 32 + 255) / 256), 256, 0, st>>>(M, K, a, tc.ea);
+    MDLS_LAUNCH_CHECK();
+    split_rows_tc_kernel<P, kTcRows, Cfg::S, AV><<<dim3((unsigned)((Mp * 32 + 255) / 256), kch), 256, 0, st>>>(
         M, Mp, K, KB16, a, tc.As, tc.ea);
     MDLS_LAUNCH_CHECK();
-    split_rows_tc_kernel<P, Cfg::NT, Cfg::SP, ViewTranspose<BV>><<<(unsigned)((Np * 32 + 255) / 256), 256, 0, st>>>(
-        N, Np, K, KB16, ViewTranspose<BV>{b}, tc.Bs, tc.fb);
+    split_scale_kernel<ViewTranspose<BV>><<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(N, K, ViewTranspose<BV>{b},
+                                                                                            tc.fb);
+    MDLS_LAUNCH_CHECK();
+    split_rows_tc_kernel<P, Cfg::NT, Cfg::SP, ViewTranspose<BV>>
+        <<<dim3((unsigned)((Np * 32 + 255) / 256), kch), 256, 0, st>>>(N, Np, K, KB16, ViewTranspose<BV>{b}, tc.Bs,
+                                                                       tc.fb);
     MDLS_LAUNCH_CHECK();
     const int64_t tiles = (Mp / kTcRows) * (Np / Cfg::NT);
     const int64_t groups = (KB16 + Cfg::DK - 1) / Cfg::DK;
+    // K split when the tiles alone leave SMs idle: the split minimising
+    // waves x groups per block (one block per SM), to at most 16 parts
     int64_t ks = 1;
     const int64_t sms = sm_count();
     if (tiles < sms && sb.ptr != nullptr && groups >= 2) {
-        ks = (sms + tiles - 1) / tiles;
-        if (ks > 16) ks = 16;
-        if (ks > groups) ks = groups;
-        while (ks > 1 && ks * M * N > sb.cap) --ks;
+        int64_t best = groups;  // one wave of whole K ranges
+        for (int64_t s = 2; s <= 16 && s <= groups; ++s) {
+            if (s * M * N > sb.cap) break;
+            const int64_t c = ((tiles * s + sms - 1) / sms) * ((groups + s - 1) / s);
+            if (c < best) {
+                best = c;
+                ks = s;
+            }
+        }
     }
     int64_t kb_per = (groups + ks - 1) / ks * Cfg::DK;
     ks = (KB16 + kb_per - 1) / kb_per;

@@ -27,6 +27,7 @@
 
 #include "common.cuh"
 #include "fx.cuh"
+#include "words.cuh"
 
 namespace mdls {
 
@@ -92,6 +93,24 @@ DEV_INLINE void md_to_digits(const double (&x)[P], int e, int (&dig)[S]) {
         carry = (v - d) >> 8;
         dig[S - 1 - b] = d;
     }
+}
+
+// The output of a split product: 2^e0 sum_g w[g] 2^(32 g) (exact, the
+// product already negated if asked), plus C's old value when `accumulate`,
+// rounded toward zero to P limbs (words.cuh).  C's value joins the words on
+// the integer pipe when its leading exponent lies inside their range, which
+// it does unless C outweighs the row-times-column scale of the product by
+// 2^32 or more; then the sum is one md addition.
+template <int P, int GW>
+DEV_INLINE md<P> split_epilogue(int64_t (&w)[GW], int e0, int accumulate, const double* base, int64_t ps,
+                                int64_t off) {
+    if (!accumulate) return words::to_md<P, GW>(w, e0, false);
+    const md<P> old = ld_md<P>(base, ps, off);
+    if (old.v[0] == 0.0 || exponent_of(old.v[0]) - e0 < 32 * (GW - 2)) {
+        words::add_md<GW, P>(w, old, e0);
+        return words::to_md<P, GW>(w, e0, false);
+    }
+    return md_add<P>(old, words::to_md<P, GW>(w, e0, false));
 }
 
 // One warp per row i of the operand view: e_i, then the S digit slices.
@@ -226,35 +245,25 @@ __global__ void __launch_bounds__(256)
         const int r = tid / kSplitTn, cc = tid % kSplitTn;
         const int64_t i = i0 + r, j = j0 + cc;
         if (i < M && j < N) {
-            // the value 2^sc sum_q D_q 2^(-8(q+2)) exactly, as 24-bit digits on
-            // the integer pipe (D_q is an integer below 2^40 in magnitude),
-            // then truncated to P limbs: no FP64 work for the S sums.  D_q
-            // sits at bit 8(S-1-q) of sum_q D_q 2^(8(S-1-q)) (compile-time
-            // digit positions); the whole sum is then shifted by the 0..23
-            // bits that put its weight 2^(sc - 8(S+1)) on a digit boundary.
-            constexpr int N = fx::Cfg<P>::N;
-            constexpr int ND = (8 * (S - 1) + 23) / 24 + 4;
-            const int sc = ea[i] + fb[j];
-            const int bmin = sc - 8 * (S + 1);  // weight of D_(S-1)
-            const int E = fx::floordiv24(bmin);
-            const int boff = bmin - 24 * E;      // 0..23
-            int64_t c[ND];
+            // the value 2^sc sum_q D_q 2^(-8(q+2)) = 2^e0 sum_q D_q 2^(8(S-1-q))
+            // exactly in 32-bit-spaced int64 words (D_q is an integer below
+            // 2^40 in magnitude: its low and high 32 bits go to adjacent
+            // words), C's old value joined on the integer pipe (words.cuh)
+            constexpr int G = (S + 3) / 4, GW = G + 3;
+            const int e0 = ea[i] + fb[j] - 8 * (S + 1);
+            int64_t w[GW];
 #pragma unroll
-            for (int k = 0; k < ND; ++k) c[k] = 0;
+            for (int k = 0; k < GW; ++k) w[k] = 0;
 #pragma unroll
             for (int q = 0; q < S; ++q) {
-                const int sh = 8 * (S - 1 - q), k = sh / 24, rem = sh % 24;
-                const int64_t dq = Dsm[(size_t)q * (kSplitTm * kSplitTn) + tid];
-                c[k] += (dq & (((int64_t)1 << (24 - rem)) - 1)) << rem;
-                c[k + 1] += dq >> (24 - rem);
+                const int sh = 8 * (S - 1 - q), k = sh / 32, rem = sh % 32;
+                int64_t dq = Dsm[(size_t)q * (kSplitTm * kSplitTn) + tid];
+                if (negate) dq = -dq;
+                w[k] += (int64_t)((uint64_t)dq & 0xffffffffULL) << rem;
+                w[k + 1] += (dq >> 32) * ((int64_t)1 << rem);
             }
-            fx::carry_norm<ND>(c);
-#pragma unroll
-            for (int k = 0; k < ND; ++k) c[k] *= (int64_t)1 << boff;
-            md<P> v = fx::xf_to_md<P, N>(fx::xf_from_acc<N, ND>(c, E));
-            if (negate) v = md_neg<P>(v);
             const int64_t off = j * C.ld + i;
-            if (accumulate) v = md_add<P>(ld_md<P>(C.ptr, C.ps, off), v);
+            const md<P> v = split_epilogue<P, GW>(w, e0, accumulate, C.ptr, C.ps, off);
             st_md<P>(C.ptr, C.ps, off, v);
         }
     }

@@ -28,8 +28,8 @@
 // diagonals per word, 2^8 apart), and the next k16 block overwrites them.
 //
 // Roles (320 threads, one block per SM): warp 8 lane 0 streams operands with
-// cp.async.bulk into a ring of A slice tiles (4 KB each) and a ring of B
-// stacks, completing on mbarriers; warp 9 lane 0 issues tcgen05.mma and
+// cp.async.bulk into a ring of stages of SB A slice tiles (4 KB each) and a
+// ring of B stacks, completing on mbarriers; warp 9 lane 0 issues tcgen05.mma and
 // tcgen05.commit; warps 0-7 read TMEM (warp w reads lanes 32 (w mod 4) ...,
 // half w / 4 of the NT columns), keep the exact words, and write the result
 // (to C, or as one md partial product when K is split over blocks).  Every
@@ -37,12 +37,15 @@
 // gives up records MDLS_ERR_TIMEOUT, lets its copies and MMAs in flight
 // finish (again bounded) and frees its TMEM before it returns.
 //
-// Operand layout (split_rows_tc_kernel): the tensor core's no-swizzle
-// K-major form, core matrices of 8 rows x 8 k (16 bytes per row) stored
-// [row tile][k16 block][slice][8-row group][k half][8 rows][8 k], so that
-// one A slice tile (128 x 16) and one B stack (SP slices x NT x 16) are each
-// one contiguous bulk copy, and in shared memory adjacent core matrices are
-// 128 bytes apart along k and 256 bytes apart along rows.
+// Operand layout (split_rows_tc_kernel): the tensor core's K-major form with
+// the 32-byte swizzle, stored [row tile][k16 block][slice][row][32 bytes]
+// (the two 16-byte halves of a row exchanged in rows 4-7 of every 8), so
+// that the A slice tiles of a k16 block (128 x 16 each, taken SB at a time)
+// and one B stack (SP slices x NT x 16) are each one contiguous bulk copy.
+// tcgen05.mma's own rate on this part (probe: M = 128, operands in shared
+// memory, back to back) is 4092 multiply-adds per clock per SM from N = 128
+// on, with a floor of about 46 cycles per instruction below it; the issuing
+// thread therefore waits on one barrier and commits once per SB slices.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -63,12 +66,16 @@ struct TcCfg {
     static constexpr int TCOLS = SP * NT;              // TMEM columns used: 240, 448, 448
     static constexpr int TALLOC = TCOLS <= 256 ? 256 : 512;
     static constexpr int CHUNK = 256 / NT;             // B slices per MMA (N <= 256)
-    static constexpr int NA = 24;                      // A slice tiles in flight
+    static constexpr int SB = 8;                       // A slices per stage (one bulk copy)
+    static constexpr int NBAT = (S + SB - 1) / SB;     // stages per k16 block
+    static constexpr int NA = 4;                       // A stages in flight
     static constexpr int NB = 2;                       // B stacks in flight
-    static constexpr int ABYTES = 128 * 16 * 2;
+    static constexpr int ABYTES = 128 * 16 * 2;        // one A slice tile
+    static constexpr int ASTAGE = SB * ABYTES;
     static constexpr int BBYTES = SP * NT * 16 * 2;
     static constexpr int NBARS = 2 * NA + 2 * NB + 3;  // full/empty rings, tmem full/empty, final
     static_assert(DK >= 1 && TCOLS <= 512, "digit diagonals must fit TMEM");
+    static_assert((size_t)HALF * G * 256 * 8 <= (size_t)NA * SB * 128 * 16 * 2, "the epilogue's words fit the A ring");
 };
 
 constexpr int kTcRows = 128;     // MMA M: one TMEM lane per output row
@@ -77,7 +84,7 @@ constexpr int kTcThreads = 320;  // 8 drain warps, a copy warp, an MMA warp
 template <int P>
 constexpr size_t split_tc_smem() {
     using C = TcCfg<P>;
-    return (size_t)C::NA * C::ABYTES + (size_t)C::NB * C::BBYTES + (size_t)C::NBARS * 8 + 16;
+    return (size_t)C::NA * C::ASTAGE + (size_t)C::NB * C::BBYTES + (size_t)C::NBARS * 8 + 16;
 }
 
 // ---------------------------------------------------------------------------
@@ -178,12 +185,13 @@ DEV_INLINE void tc_ld<8>(uint32_t taddr, float (&v)[8]) {
     for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// Shared-memory matrix descriptor: no swizzle, K-major, core matrices of
-// 8 rows x 16 bytes; leading (k) byte offset 128, stride (8-row group) byte
-// offset 256; bits 46-48 hold the fixed value 0b001.
+// Shared-memory matrix descriptor: K-major with the 32-byte swizzle (mode 6
+// in bits 61-63): rows of 32 bytes (one k16 block), 8-row groups 256 bytes
+// apart (stride byte offset), leading byte offset unused (16); bits 46-48
+// hold the fixed value 0b001.  Every tile starts on a 256-byte boundary.
 DEV_INLINE uint64_t tc_smem_desc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
-           ((uint64_t)1 << 46);
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
 }
 // Instruction descriptor of kind::f16: fp32 D (bits 4-5 = 1), bf16 A and B
 // (bits 7-9 and 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
@@ -195,46 +203,110 @@ __host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N) {
 // ---------------------------------------------------------------------------
 // Digit slices in the tiled layout
 // ---------------------------------------------------------------------------
-// One warp per row i < Rp of the operand view (rows R .. Rp-1 and k >= K
-// are zero): the row's power-of-two scale e_i, then its S digits at every k
-// < 16 KB16, written to [i / RT][k / 16][s][(i mod RT) / 8][(k / 8) mod 2]
-// [i mod 8][k mod 8]; slices S .. SP-1 are zero.
+// One warp per row i < R of the operand view: the row's power-of-two scale
+// e_i (its largest leading-limb exponent + 3, so every scaled entry lies
+// below 1/4 in magnitude).
+template <class AV>
+__global__ void split_scale_kernel(int64_t R, int64_t K, AV A, int* scale) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= R) return;
+    int emax = -100000;
+    for (int64_t k = lane; k < K; k += 32) {
+        const double x0 = A.get(i, k, 0);
+        if (x0 != 0.0) emax = max(emax, exponent_of(x0));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    if (lane == 0) scale[i] = (emax == -100000) ? 0 : emax + 3;
+}
+
+constexpr int kTcConvK = 128;  // k values per warp of the digit conversion
+
+// One warp per (row i < Rp, k chunk blockIdx.y of kTcConvK values): the S
+// digits of every entry (rows R .. Rp-1 and k >= K are zero), written to
+// [i / RT][k / 16][s][i mod RT][32 bytes] with the 32-byte swizzle (the two
+// 16-byte halves of a row exchanged in rows 4-7 of every 8); slices S .. SP-1
+// are zero.
 template <int P, int RT, int SP, class AV>
 __global__ void split_rows_tc_kernel(int64_t R, int64_t Rp, int64_t K, int64_t KB16, AV A, __nv_bfloat16* out,
-                                     int* scale) {
+                                     const int* scale) {
     constexpr int S = SplitCfg<P>::S;
     constexpr int64_t kSliceStride = (int64_t)RT * 16;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= Rp) return;
     const bool live = i < R;
-    int emax = -100000;
-    if (live)
-        for (int64_t k = lane; k < K; k += 32) {
-            const double x0 = A.get(i, k, 0);
-            if (x0 != 0.0) emax = max(emax, exponent_of(x0));
-        }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
-    const int e = (emax == -100000) ? 0 : emax + 3;
-    if (live && lane == 0) scale[i] = e;
+    const int e = live ? scale[i] : 0;
     const int64_t rt = i / RT;
     const int r = (int)(i % RT);
     const int64_t Kp = KB16 * 16;
-    for (int64_t k = lane; k < Kp; k += 32) {
+    const int64_t kend = ((int64_t)blockIdx.y + 1) * kTcConvK < Kp ? ((int64_t)blockIdx.y + 1) * kTcConvK : Kp;
+    for (int64_t k = (int64_t)blockIdx.y * kTcConvK + lane; k < kend; k += 32) {
         double x[P];
 #pragma unroll
         for (int l = 0; l < P; ++l) x[l] = (live && k < K) ? A.get(i, k, l) : 0.0;
         int dig[S];
         md_to_digits<P, S>(x, e, dig);
         const int64_t kb = k >> 4;
-        __nv_bfloat16* o = out + ((rt * KB16 + kb) * SP) * kSliceStride + (r >> 3) * 128 + ((k >> 3) & 1) * 64 +
-                           (r & 7) * 8 + (k & 7);
+        __nv_bfloat16* o = out + ((rt * KB16 + kb) * SP) * kSliceStride + r * 16 +
+                           ((((int)(k >> 3) & 1) ^ ((r >> 2) & 1)) * 8) + (k & 7);
 #pragma unroll
         for (int s = 0; s < S; ++s) o[s * kSliceStride] = __int2bfloat16_rn(dig[s]);
 #pragma unroll
         for (int s = S; s < SP; ++s) o[s * kSliceStride] = __int2bfloat16_rn(0);
     }
+}
+
+// ---------------------------------------------------------------------------
+// The MMAs of one k16 block, unrolled at compile time
+// ---------------------------------------------------------------------------
+// Slice s of stage b (s = b SB + j) against the B stack's slices t0 ...
+// t0 + ns - 1 into TMEM columns (s + t0) NT ...: every offset and every
+// instruction descriptor is a constant, so the one issuing thread spends a
+// few instructions per MMA (the tensor core's own pace is 46-128 cycles per
+// MMA here; a loop computing them took about 200).
+template <int P, int J, int T0>
+DEV_INLINE void tc_issue_chunks(uint32_t tbase, uint64_t ad, uint64_t bd0, uint32_t acc_s0, int s) {
+    using Cfg = TcCfg<P>;
+    constexpr int S = Cfg::S, NT = Cfg::NT;
+    if constexpr (T0 < S) {
+        const int rem = S - s - T0;
+        if (rem > 0) {
+            // s is a compile-time value after unrolling; rem, ns fold with it
+            int ns = rem < Cfg::CHUNK ? rem : Cfg::CHUNK;
+            if (NT == 8 && (ns & 1)) ++ns;  // N a multiple of 16
+            tc_mma_bf16(tbase + (uint32_t)((s + T0) * NT), ad, bd0 + (uint64_t)(T0 * (NT * 32 >> 4)),
+                        tc_idesc_bf16(kTcRows, ns * NT), s == 0 ? acc_s0 : 1u);
+            tc_issue_chunks<P, J, T0 + Cfg::CHUNK>(tbase, ad, bd0, acc_s0, s);
+        }
+    }
+}
+
+template <int P, int B, int J>
+DEV_INLINE void tc_issue_stage(uint32_t tbase, uint64_t ad0, uint64_t bd0, uint32_t acc_s0) {
+    using Cfg = TcCfg<P>;
+    if constexpr (J < Cfg::SB && B * Cfg::SB + J < Cfg::S) {
+        tc_issue_chunks<P, J, 0>(tbase, ad0 + (uint64_t)(J * (Cfg::ABYTES >> 4)), bd0, acc_s0, B * Cfg::SB + J);
+        tc_issue_stage<P, B, J + 1>(tbase, ad0, bd0, acc_s0);
+    }
+}
+
+// Stages B ... NBAT-1 of one k16 block: wait for the stage, issue its MMAs,
+// commit it back to the copy warp.  False when a wait gave up.
+template <int P, int B>
+DEV_INLINE bool tc_issue_k16(uint32_t tbase, uint32_t sA0, uint64_t bd0, uint32_t acc_s0, uint32_t& ia,
+                             uint32_t bar0, unsigned long long lim, volatile int* abort_flag) {
+    using Cfg = TcCfg<P>;
+    if constexpr (B < Cfg::NBAT) {
+        const uint32_t sa = ia % Cfg::NA;
+        if (!mbar_wait(bar0 + 8u * sa, (ia / Cfg::NA) & 1, lim, abort_flag)) return false;
+        tc_issue_stage<P, B, 0>(tbase, tc_smem_desc(sA0 + sa * Cfg::ASTAGE), bd0, acc_s0);
+        tc_commit(bar0 + 8u * (Cfg::NA + sa));
+        ++ia;
+        return tc_issue_k16<P, B + 1>(tbase, sA0, bd0, acc_s0, ia, bar0, lim, abort_flag);
+    }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -256,7 +328,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     constexpr int NA = Cfg::NA, NB = Cfg::NB;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char* sA = tc_smem;
-    unsigned char* sB = sA + NA * Cfg::ABYTES;
+    unsigned char* sB = sA + NA * Cfg::ASTAGE;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sB + NB * Cfg::BBYTES);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + Cfg::NBARS);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
@@ -301,7 +373,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(tslot);
 
     if (warp == 8) {
-        // ---- copies: per k16 block the B stack, then the S slice tiles of A
+        // ---- copies: per k16 block the B stack, then the A slice tiles in
+        //      stages of SB (contiguous in the tiled layout: one copy each)
         if (lane == 0 && kb1 > kb0) {
             uint32_t ia = 0, ib = 0;
             bool ok = true;
@@ -312,12 +385,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 bulk_copy_g2s(sB0 + sb * Cfg::BBYTES, Bs + ((nt * KB16 + kb) * SP) * (NT * 16), Cfg::BBYTES,
                               fullB(sb));
                 ++ib;
-                for (int s = 0; s < S; ++s) {
+                for (int s0 = 0; s0 < S; s0 += Cfg::SB) {
+                    const int ns = (S - s0 < Cfg::SB) ? S - s0 : Cfg::SB;
                     const uint32_t sa = ia % NA;
                     if (!(ok = mbar_wait(emptyA(sa), ((ia / NA) & 1) ^ 1, lim, abort_flag))) break;
-                    mbar_expect_tx(fullA(sa), Cfg::ABYTES);
-                    bulk_copy_g2s(sA0 + sa * Cfg::ABYTES, As + (((mt * KB16 + kb) * S) + s) * (kTcRows * 16),
-                                  Cfg::ABYTES, fullA(sa));
+                    mbar_expect_tx(fullA(sa), (uint32_t)ns * Cfg::ABYTES);
+                    bulk_copy_g2s(sA0 + sa * Cfg::ASTAGE, As + (((mt * KB16 + kb) * S) + s0) * (kTcRows * 16),
+                                  (uint32_t)ns * Cfg::ABYTES, fullA(sa));
                     ++ia;
                 }
             }
@@ -332,7 +406,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
     } else if (warp == 9) {
-        // ---- MMAs: one per A slice (two where N would pass 256)
+        // ---- MMAs: one per A slice (two where N would pass 256); one wait
+        //      and one commit per stage of SB slices
         if (lane == 0) {
             uint32_t ia = 0, ib = 0, grp = 0;
             bool ok = kb1 > kb0;
@@ -346,23 +421,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const uint32_t sb = ib % NB;
                 if (!(ok = mbar_wait(fullB(sb), (ib / NB) & 1, lim, abort_flag))) break;
                 tc_fence_after();
-                for (int s = 0; s < S; ++s) {
-                    const uint32_t sa = ia % NA;
-                    if (!(ok = mbar_wait(fullA(sa), (ia / NA) & 1, lim, abort_flag))) break;
-                    tc_fence_after();
-                    const uint64_t ad = tc_smem_desc(sA0 + sa * Cfg::ABYTES);
-                    for (int t0 = 0; t0 < S - s; t0 += Cfg::CHUNK) {
-                        int ns = S - s - t0;
-                        if (ns > Cfg::CHUNK) ns = Cfg::CHUNK;
-                        if (NT == 8 && (ns & 1)) ++ns;  // N a multiple of 16
-                        const uint64_t bd = tc_smem_desc(sB0 + sb * Cfg::BBYTES + (uint32_t)t0 * (NT * 32));
-                        tc_mma_bf16(tbase + (uint32_t)((s + t0) * NT), ad, bd, tc_idesc_bf16(kTcRows, ns * NT),
-                                    (gfirst && s == 0) ? 0u : 1u);
-                    }
-                    tc_commit(emptyA(sa));
-                    ++ia;
-                }
-                if (!ok) break;
+                // the start-address field is the descriptor's low bits: a
+                // byte offset o moves it by o >> 4
+                const uint64_t bd0 = tc_smem_desc(sB0 + sb * Cfg::BBYTES);
+                if (!(ok = tc_issue_k16<P, 0>(tbase, sA0, bd0, gfirst ? 0u : 1u, ia, bar0, lim, abort_flag))) break;
                 tc_commit(emptyB(sb));
                 ++ib;
                 if (glast) {
@@ -415,44 +477,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (lane == 0) mbar_arrive(tempty);
         }
         if (ok) {
+            // every MMA has completed and every copy has landed, so the A
+            // ring is free: the words go there (thread-private slots), and
+            // one rolled copy of the conversion serves the thread's columns
+            // (unrolled per column, the conversion code outgrew the
+            // instruction cache)
+            int64_t* sW = reinterpret_cast<int64_t*>(sA) + (threadIdx.x & 255);
+#pragma unroll
+            for (int j = 0; j < HALF; ++j)
+#pragma unroll
+                for (int g = 0; g < G; ++g) sW[(j * G + g) * 256] = negate ? -W[g][j] : W[g][j];
             const int64_t i = mt * kTcRows + 32 * quarter + lane;
             if (i < M) {
-                constexpr int NX = fx::Cfg<P>::N;
-                constexpr int ND = (32 * (G - 1)) / 24 + 6;
                 const int sci = ea[i];
-#pragma unroll
+                double* base = C.ptr + (int64_t)blockIdx.y * part_stride;
+#pragma unroll 1
                 for (int j = 0; j < HALF; ++j) {
                     const int64_t jc = nt * NT + half * HALF + j;
-                    if (jc >= N) continue;
-                    // value = 2^(sc - 8(S+1)) sum_g W_g 2^(32 g): placed in
-                    // 24-bit digits, then shifted onto a digit boundary
-                    const int bmin = sci + fb[jc] - 8 * (S + 1);
-                    const int E = fx::floordiv24(bmin);
-                    const int boff = bmin - 24 * E;
-                    int64_t c[ND];
+                    if (jc >= N) break;
+                    // value = 2^e0 sum_g W_g 2^(32 g) exactly (D_q at bit
+                    // 8 (S-1-q)); C's old value joins it on the integer pipe
+                    const int e0 = sci + fb[jc] - 8 * (S + 1);
+                    int64_t w[G + 3];
 #pragma unroll
-                    for (int k = 0; k < ND; ++k) c[k] = 0;
+                    for (int g = 0; g < G; ++g) w[g] = sW[(j * G + g) * 256];
 #pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        const int sh = 32 * g, k = sh / 24, rem = sh % 24;
-                        int64_t w = W[g][j];
-                        c[k] += (w & (((int64_t)1 << (24 - rem)) - 1)) << rem;
-                        w >>= (24 - rem);
-                        c[k + 1] += w & fx::kMask;
-                        w >>= 24;
-                        c[k + 2] += w & fx::kMask;
-                        w >>= 24;
-                        c[k + 3] += w;
-                    }
-                    fx::carry_norm<ND>(c);
-#pragma unroll
-                    for (int k = 0; k < ND; ++k) c[k] *= (int64_t)1 << boff;
-                    md<P> v = fx::xf_to_md<P, NX>(fx::xf_from_acc<NX, ND>(c, E));
-                    if (negate) v = md_neg<P>(v);
-                    double* base = C.ptr + (int64_t)blockIdx.y * part_stride;
-                    const int64_t off = jc * C.ld + i;
-                    if (accumulate) v = md_add<P>(ld_md<P>(base, C.ps, off), v);
-                    st_md<P>(base, C.ps, off, v);
+                    for (int g = G; g < G + 3; ++g) w[g] = 0;
+                    st_md<P>(base, C.ps, jc * C.ld + i,
+                             split_epilogue<P, G + 3>(w, e0, accumulate, base, C.ps, jc * C.ld + i));
                 }
             }
         }
