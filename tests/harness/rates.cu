@@ -8,6 +8,8 @@
 //   out[0] DFMA (FP64 instructions/s), out[1] DADD, out[2] FFMA, out[3] IMAD,
 //   out[4] HMMA bf16 m16n8k16 (flop/s), out[5] IMMA s8 m16n8k32 (op/s),
 //   out[6] DMMA f64 m8n8k4 (flop/s).
+// probe_tcgen05() gives the cycles per tcgen05.mma kind::f16 (M = 128) of
+// the split products' operand layout at N = 16, 64, 128, 256.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -137,6 +139,109 @@ __global__ void dmma_kernel(double* out, double s) {
 }
 
 }  // namespace
+
+// tcgen05.mma (kind::f16, bf16 operands, fp32 accumulators in tensor memory,
+// cta_group::1, M = 128) issued back to back by one thread per block, one
+// block per SM, A and B read from shared memory in the 32-byte-swizzled
+// K-major layout of the split products, rotating over 8 A tiles and 8 B
+// regions so that every MMA reads fresh operands.  The issuing thread waits
+// for completion on an mbarrier (bounded: 2 s of the global timer) and
+// records clock64 cycles; every block frees its tensor memory before it
+// returns.
+static __device__ __forceinline__ uint32_t tc_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+static __device__ __forceinline__ unsigned long long tc_gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+static __device__ __forceinline__ uint64_t tc_desc(uint32_t a) {
+    return (uint64_t)((a >> 4) & 0x3FFF) | (1ull << 16) | ((uint64_t)16 << 32) | (1ull << 46) | (6ull << 61);
+}
+
+static __global__ void __launch_bounds__(128, 1) tcgen05_rate_kernel(int R, int N, unsigned long long* cycles) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* A = sm;          // 8 tiles of 128 x 32 bytes
+    unsigned char* B = sm + 32768;  // 8 regions of 256 x 32 bytes
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 98304);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + 98304 + 16);
+    for (int i = threadIdx.x; i < 98304 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(sm)[i] = 0x3f803f80u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_saddr(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(tc_saddr(slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(slot);
+    if (threadIdx.x == 0) {
+        const uint64_t ad = tc_desc(tc_saddr(A)), bd = tc_desc(tc_saddr(B));
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | (8u << 24);
+        const unsigned long long t0 = clock64();
+        for (int r = 0; r < R; ++r) {
+            const uint64_t rot = (uint64_t)(r & 7);
+            const uint32_t acc = r > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad + rot * 256), "l"(bd + rot * 512), "r"(idesc), "r"(acc)
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         tc_saddr(bar))
+                     : "memory");
+        uint32_t ok = 0;
+        const unsigned long long g0 = tc_gtimer();
+        while (!ok && tc_gtimer() - g0 < 2000000000ull)
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(ok)
+                : "r"(tc_saddr(bar))
+                : "memory");
+        cycles[blockIdx.x] = ok ? clock64() - t0 : 0ull;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    }
+}
+
+// Cycles per tcgen05.mma (the slowest block's average over R = 4096) for
+// N = 16, 64, 128, 256 in out[0..3]; 0 when a block's wait gave up.
+extern "C" int probe_tcgen05(double* out, int nout) {
+    int sms = 0;
+    if (nout < 4 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) return -1;
+    const size_t smem = 98304 + 64;
+    if (cudaFuncSetAttribute(tcgen05_rate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return -1;
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned long long) * sms) != cudaSuccess) return -1;
+    unsigned long long h[1024];
+    const int Ns[4] = {16, 64, 128, 256};
+    const int R = 4096;
+    int rc = 0;
+    for (int k = 0; k < 4 && rc == 0; ++k) {
+        for (int w = 0; w < 2; ++w) tcgen05_rate_kernel<<<sms, 128, smem>>>(R, Ns[k], d);
+        if (cudaDeviceSynchronize() != cudaSuccess) { rc = -1; break; }
+        cudaMemcpy(h, d, sizeof(unsigned long long) * (sms < 1024 ? sms : 1024), cudaMemcpyDeviceToHost);
+        unsigned long long mx = 0;
+        for (int i = 0; i < sms && i < 1024; ++i) {
+            if (h[i] == 0) rc = -2;
+            mx = h[i] > mx ? h[i] : mx;
+        }
+        out[k] = (double)mx / R;
+    }
+    cudaFree(d);
+    return rc;
+}
 
 extern "C" int probe_rates(double* out, int nout) {
     if (nout < 7) return -1;

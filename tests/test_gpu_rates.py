@@ -1,6 +1,8 @@
 """Measured throughput of the GB300 pipes the multiple-double path can use
 (tests/harness/rates.cu): FP64 DFMA/DADD instructions, FP32 FFMA, INT32 IMAD,
-and the warp-level matrix instructions mma.sync for bf16, int8 and f64.
+the warp-level matrix instructions mma.sync for bf16, int8 and f64, and
+tcgen05.mma kind::f16 (M = 128, operands in shared memory in the split
+products' layout) at N = 16 ... 256.
 These rates set the roofline denominators of the md kernels (FP64
 instructions per second) and decide which pipe the split products use.
 Run with -s to see the numbers."""
@@ -34,3 +36,10 @@ def test_pipe_rates():
     # the FP64 issue rate the md rooflines use: 2 instructions/clk/SM x 152 SMs
     # x 2.07 GHz = 0.629 T/s; a probe far from it would make those fractions wrong
     assert 0.3e12 < r[0] < 0.8e12
+    L.probe_tcgen05.argtypes = [C.POINTER(C.c_double), C.c_int]
+    t = (C.c_double * 4)()
+    assert L.probe_tcgen05(t, 4) == 0
+    for n, cyc in zip((16, 64, 128, 256), t):
+        print(f"tcgen05.mma kind::f16 M=128 N={n:3d}: {cyc:7.1f} cycles, {128 * n * 16 / cyc:7.0f} MAC/clk/SM")
+    # 128 x 256 x 16 at the nominal bf16 rate (about 4096 MAC/clk/SM) is 128 cycles
+    assert 100 < t[3] < 400 and t[0] <= t[3]
