@@ -178,7 +178,7 @@ def paper_equivalent(precs, n, per_prec_ms, steps):
     return out
 
 
-def cpu_baseline(n_sample: int, precs, seed: int = 0) -> dict:
+def cpu_baseline(n_sample: int, precs, seed: int = 0, single_core: bool = True) -> dict:
     """The oracle (plain C, OpenMP) on a bounded sample of the workload: the
     leading n_sample x n_sample block of each precision's A and the leading
     n_sample entries of b, solved in every precision."""
@@ -196,10 +196,26 @@ def cpu_baseline(n_sample: int, precs, seed: int = 0) -> dict:
         oracle.lstsq(As, bs)
         flops += opcount.lstsq_table1_flops(p, n_sample, n_sample)
     dt = time.perf_counter() - t0
-    return {"value": flops / dt / 1e12, "unit": "TFLOPS", "cores": cores, "kind": "oracle",
-            "sample": f"lstsq of the leading {n_sample}x{n_sample} block of the n=1024 inputs, "
-                      f"precisions {','.join(PREC_NAMES[p] for p in precs)}; {dt:.1f} s",
-            "seconds": dt}
+    out = {"value": flops / dt / 1e12, "unit": "TFLOPS", "cores": cores, "kind": "oracle",
+           "sample": f"lstsq of the leading {n_sample}x{n_sample} block of the n=1024 inputs, "
+                     f"precisions {','.join(PREC_NAMES[p] for p in precs)}; {dt:.1f} s",
+           "seconds": dt}
+    if not single_core:
+        return out
+    # the same oracle on one core, on a smaller block (its time grows as n^3)
+    n1 = max(16, n_sample * 5 // 14)
+    oracle.set_threads(1)
+    flops1 = 0
+    t1 = time.perf_counter()
+    for p in precs:
+        A, b = synth.lstsq_problem(p, 1024, 1024, seed=seed, tag="cfg1")
+        oracle.lstsq(A[:, :n1, :n1].copy(), b[:, :n1].copy())
+        flops1 += opcount.lstsq_table1_flops(p, n1, n1)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
+    out["single_core"] = {"value": flops1 / dt1 / 1e12, "unit": "TFLOPS", "cores": 1,
+                          "sample": f"lstsq of the leading {n1}x{n1} block, same precisions; {dt1:.1f} s"}
+    return out
 
 
 def run_reference(args):
@@ -210,10 +226,10 @@ def run_reference(args):
         return
     n_sample = 256
     for _ in range(args.warmup):
-        cpu_baseline(n_sample, precs)
+        cpu_baseline(n_sample, precs, single_core=False)
     vals, secs = [], 0.0
     for _ in range(args.steps):
-        r = cpu_baseline(n_sample, precs)
+        r = cpu_baseline(n_sample, precs, single_core=False)
         vals.append(r["value"])
         secs += r["seconds"]
     value = statistics.mean(vals)
