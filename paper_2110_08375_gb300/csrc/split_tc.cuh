@@ -10,15 +10,19 @@
 //
 // Diagonals as columns.  For a 128 x NT output tile, TMEM holds one fp32
 // accumulator column per (diagonal q, output column j), at column q NT + j.
-// Slice s of A (128 rows x 16 k, one k16 block) multiplies the stack
-// [B_0; B_1; ...; B_{S-1-s}] of B's slices (N = (S-s) NT rows of the B
-// operand) into TMEM columns s NT ... S NT - 1: row t NT + j of the stack is
-// B_t(:, j), whose product with A_s belongs to diagonal s + t.  One MMA per
-// A slice (two where N would exceed 256) therefore produces every pair
-// (s, t) with s + t < S and nothing else: S(S+1)/2 slice products per k,
-// as many as the pairwise form, in MMAs of N up to 256.  For octo double
-// NT = 8 and an odd stack gets one more slice so that N is a multiple of
-// 16; its products land in column group S, which is never read.
+// Slice s of A (128 rows x 16 k, one k16 block) multiplies a run of the
+// stack [B_0; B_1; ...] of B's slices (row t NT + j of the stack is
+// B_t(:, j), whose product with A_s belongs to diagonal s + t) into the TMEM
+// columns of the diagonals it reaches.  Each k16 block runs two passes: the
+// low pass gives slice s < Q the diagonals s .. Q-1, the high pass gives
+// every slice the diagonals max(s, Q) .. S-1, one MMA per slice and pass, so
+// the pairs (s, t) with s + t < S are each formed once: S(S+1)/2 slice
+// products per k, as many as the pairwise form.  The low diagonals are then
+// complete before the high pass starts: their drain runs beside it, and the
+// high diagonals drain beside the next block's low pass.  For octo double
+// NT = 8; an odd run is padded to a multiple of 16 columns downward with a
+// zero slice kept in front of the stack (exact zeros added) or upward into
+// column group S, which is never read.
 //
 // Exactness.  |d_a d_b| <= 2^14 and a column of diagonal q gains (q + 1) 16
 // products per k16 block, so after DK = floor(1024 / (16 S)) blocks every
@@ -28,8 +32,9 @@
 // diagonals per word, 2^8 apart), and the next k16 block overwrites them.
 //
 // Roles (320 threads, one block per SM): warp 8 lane 0 streams operands with
-// cp.async.bulk into a ring of stages of SB A slice tiles (4 KB each) and a
-// ring of B stacks, completing on mbarriers; warp 9 lane 0 issues tcgen05.mma and
+// cp.async.bulk into a ring of stages of SB A slice tiles (4 KB each; the low
+// pass's stages stay in until the high pass has read them again) and a ring
+// of B stacks, completing on mbarriers; warp 9 lane 0 issues tcgen05.mma and
 // tcgen05.commit; warps 0-7 read TMEM (warp w reads lanes 32 (w mod 4) ...,
 // half w / 4 of the NT columns), keep the exact words, and write the result
 // (to C, or as one md partial product when K is split over blocks).  Every
@@ -65,15 +70,20 @@ struct TcCfg {
     static constexpr int HALF = NT / 2;                // columns per drain thread
     static constexpr int TCOLS = SP * NT;              // TMEM columns used: 240, 448, 448
     static constexpr int TALLOC = TCOLS <= 256 ? 256 : 512;
-    static constexpr int CHUNK = 256 / NT;             // B slices per MMA (N <= 256)
     static constexpr int SB = 8;                       // A slices per stage (one bulk copy)
     static constexpr int NBAT = (S + SB - 1) / SB;     // stages per k16 block
-    static constexpr int NA = 4;                       // A stages in flight
+    static constexpr int Q = P == 8 ? 32 : (P == 4 ? 16 : 8);  // low diagonals: q < Q
+    static constexpr int QS = Q / SB;                  // stages of the low pass
+    static constexpr int NA = 6;                       // A stages in flight
     static constexpr int NB = 2;                       // B stacks in flight
+    static constexpr int ZP = NT == 8 ? 1 : 0;         // zero slices in front of a B stack
     static constexpr int ABYTES = 128 * 16 * 2;        // one A slice tile
     static constexpr int ASTAGE = SB * ABYTES;
-    static constexpr int BBYTES = SP * NT * 16 * 2;
-    static constexpr int NBARS = 2 * NA + 2 * NB + 3;  // full/empty rings, tmem full/empty, final
+    static constexpr int BCOPY = SP * NT * 16 * 2;     // one B stack as copied
+    static constexpr int BBYTES = (ZP + SP) * NT * 16 * 2;
+    static constexpr int NBARS = 2 * NA + 2 * NB + 5;  // full/empty rings, tmem full/empty x 2, final
+    static_assert(Q % SB == 0 && Q < S && QS < NA, "the low pass's stages stay resident beside one more");
+    static_assert(Q * NT <= 256 && (S - Q + 1) * NT <= 256, "one MMA per slice and pass");
     static_assert(DK >= 1 && TCOLS <= 512, "digit diagonals must fit TMEM");
     static_assert((size_t)HALF * G * 256 * 8 <= (size_t)NA * SB * 128 * 16 * 2, "the epilogue's words fit the A ring");
 };
@@ -259,54 +269,110 @@ __global__ void split_rows_tc_kernel(int64_t R, int64_t Rp, int64_t K, int64_t K
 }
 
 // ---------------------------------------------------------------------------
-// The MMAs of one k16 block, unrolled at compile time
+// The MMAs of one k16 block, unrolled at compile time, in two passes
 // ---------------------------------------------------------------------------
-// Slice s of stage b (s = b SB + j) against the B stack's slices t0 ...
-// t0 + ns - 1 into TMEM columns (s + t0) NT ...: every offset and every
-// instruction descriptor is a constant, so the one issuing thread spends a
-// few instructions per MMA (the tensor core's own pace is 46-128 cycles per
-// MMA here; a loop computing them took about 200).
-template <int P, int J, int T0>
-DEV_INLINE void tc_issue_chunks(uint32_t tbase, uint64_t ad, uint64_t bd0, uint32_t acc_s0, int s) {
+// Every offset and instruction descriptor is a constant, so the one issuing
+// thread spends a few instructions per MMA (the tensor core's own pace is
+// 61-128 cycles per MMA here; a loop computing them took about 200).
+//
+// Low pass: slice s < Q against the stack slices 0 .. Q-1-s, into the low
+// diagonals s .. Q-1 (octo double pads an odd count downward with the zero
+// slice in front of the stack: diagonal s-1 gains exact zeros).  High pass:
+// every slice s against the stack slices from max(s, Q) - s on, into the
+// high diagonals max(s, Q) .. S-1 (an odd count padded upward into the
+// unread column group S).  Each pass is one MMA per slice.  The low
+// diagonals are complete after the low pass, so their drain runs beside the
+// high pass, and the high diagonals drain beside the next block's low pass.
+template <int P, int S0>
+DEV_INLINE void tc_issue_low_slice(uint32_t tbase, uint64_t ad, uint64_t bd0, uint32_t acc_s0) {
     using Cfg = TcCfg<P>;
-    constexpr int S = Cfg::S, NT = Cfg::NT;
-    if constexpr (T0 < S) {
-        const int rem = S - s - T0;
-        if (rem > 0) {
-            // s is a compile-time value after unrolling; rem, ns fold with it
-            int ns = rem < Cfg::CHUNK ? rem : Cfg::CHUNK;
-            if (NT == 8 && (ns & 1)) ++ns;  // N a multiple of 16
-            tc_mma_bf16(tbase + (uint32_t)((s + T0) * NT), ad, bd0 + (uint64_t)(T0 * (NT * 32 >> 4)),
-                        tc_idesc_bf16(kTcRows, ns * NT), s == 0 ? acc_s0 : 1u);
-            tc_issue_chunks<P, J, T0 + Cfg::CHUNK>(tbase, ad, bd0, acc_s0, s);
-        }
-    }
+    constexpr int NT = Cfg::NT;
+    constexpr int ns0 = Cfg::Q - S0;
+    constexpr int pad = (NT == 8 && (ns0 & 1)) ? 1 : 0;  // S0 odd, so S0 - 1 >= 0
+    constexpr int t0 = -pad, ns = ns0 + pad;
+    tc_mma_bf16(tbase + (uint32_t)((S0 + t0) * NT), ad, bd0 + (uint64_t)((Cfg::ZP + t0) * (NT * 32 >> 4)),
+                tc_idesc_bf16(kTcRows, ns * NT), S0 == 0 ? acc_s0 : 1u);
 }
 
-template <int P, int B, int J>
+template <int P, int S0>
+DEV_INLINE void tc_issue_high_slice(uint32_t tbase, uint64_t ad, uint64_t bd0, uint32_t acc_s0) {
+    using Cfg = TcCfg<P>;
+    constexpr int NT = Cfg::NT, S = Cfg::S;
+    constexpr int q0 = S0 > Cfg::Q ? S0 : Cfg::Q;
+    constexpr int t0 = q0 - S0, ns0 = S - q0;
+    constexpr int ns = (NT == 8 && (ns0 & 1)) ? ns0 + 1 : ns0;
+    tc_mma_bf16(tbase + (uint32_t)(q0 * NT), ad, bd0 + (uint64_t)((Cfg::ZP + t0) * (NT * 32 >> 4)),
+                tc_idesc_bf16(kTcRows, ns * NT), S0 == 0 ? acc_s0 : 1u);
+}
+
+template <int P, bool HIGH, int B, int J>
 DEV_INLINE void tc_issue_stage(uint32_t tbase, uint64_t ad0, uint64_t bd0, uint32_t acc_s0) {
     using Cfg = TcCfg<P>;
-    if constexpr (J < Cfg::SB && B * Cfg::SB + J < Cfg::S) {
-        tc_issue_chunks<P, J, 0>(tbase, ad0 + (uint64_t)(J * (Cfg::ABYTES >> 4)), bd0, acc_s0, B * Cfg::SB + J);
-        tc_issue_stage<P, B, J + 1>(tbase, ad0, bd0, acc_s0);
+    constexpr int S0 = B * Cfg::SB + J;
+    if constexpr (J < Cfg::SB && S0 < (HIGH ? Cfg::S : Cfg::Q)) {
+        const uint64_t ad = ad0 + (uint64_t)(J * (Cfg::ABYTES >> 4));
+        if constexpr (HIGH)
+            tc_issue_high_slice<P, S0>(tbase, ad, bd0, acc_s0);
+        else
+            tc_issue_low_slice<P, S0>(tbase, ad, bd0, acc_s0);
+        tc_issue_stage<P, HIGH, B, J + 1>(tbase, ad0, bd0, acc_s0);
     }
 }
 
-// Stages B ... NBAT-1 of one k16 block: wait for the stage, issue its MMAs,
-// commit it back to the copy warp.  False when a wait gave up.
+// The low pass over stages B .. QS-1 of the block whose first stage is ia:
+// wait for each (first use), issue, keep it (the high pass reads it again).
 template <int P, int B>
-DEV_INLINE bool tc_issue_k16(uint32_t tbase, uint32_t sA0, uint64_t bd0, uint32_t acc_s0, uint32_t& ia,
+DEV_INLINE bool tc_issue_low(uint32_t tbase, uint32_t sA0, uint64_t bd0, uint32_t acc_s0, uint32_t ia,
                              uint32_t bar0, unsigned long long lim, volatile int* abort_flag) {
     using Cfg = TcCfg<P>;
-    if constexpr (B < Cfg::NBAT) {
-        const uint32_t sa = ia % Cfg::NA;
-        if (!mbar_wait(bar0 + 8u * sa, (ia / Cfg::NA) & 1, lim, abort_flag)) return false;
-        tc_issue_stage<P, B, 0>(tbase, tc_smem_desc(sA0 + sa * Cfg::ASTAGE), bd0, acc_s0);
-        tc_commit(bar0 + 8u * (Cfg::NA + sa));
-        ++ia;
-        return tc_issue_k16<P, B + 1>(tbase, sA0, bd0, acc_s0, ia, bar0, lim, abort_flag);
+    if constexpr (B < Cfg::QS) {
+        const uint32_t st = ia + B, sa = st % Cfg::NA;
+        if (!mbar_wait(bar0 + 8u * sa, (st / Cfg::NA) & 1, lim, abort_flag)) return false;
+        tc_issue_stage<P, false, B, 0>(tbase, tc_smem_desc(sA0 + sa * Cfg::ASTAGE), bd0, acc_s0);
+        return tc_issue_low<P, B + 1>(tbase, sA0, bd0, acc_s0, ia, bar0, lim, abort_flag);
     }
     return true;
+}
+
+// The high pass over stages B .. NBAT-1: the low pass's stages are already
+// in, the others are waited for; every stage goes back to the copy warp
+// after its high MMAs.
+template <int P, int B>
+DEV_INLINE bool tc_issue_high(uint32_t tbase, uint32_t sA0, uint64_t bd0, uint32_t acc_s0, uint32_t ia,
+                              uint32_t bar0, unsigned long long lim, volatile int* abort_flag) {
+    using Cfg = TcCfg<P>;
+    if constexpr (B < Cfg::NBAT) {
+        const uint32_t st = ia + B, sa = st % Cfg::NA;
+        if (B >= Cfg::QS && !mbar_wait(bar0 + 8u * sa, (st / Cfg::NA) & 1, lim, abort_flag)) return false;
+        tc_issue_stage<P, true, B, 0>(tbase, tc_smem_desc(sA0 + sa * Cfg::ASTAGE), bd0, acc_s0);
+        tc_commit(bar0 + 8u * (Cfg::NA + sa));
+        return tc_issue_high<P, B + 1>(tbase, sA0, bd0, acc_s0, ia, bar0, lim, abort_flag);
+    }
+    return true;
+}
+
+// Drain of the diagonals Q0 .. Q1-1 of this thread's TMEM row: four
+// tcgen05.ld per wait, each value (an integer below 2^24 in magnitude, exact
+// in fp32) added into its int64 word (D_q at bit 8 (S-1-q)).
+template <int P, int Q0, int Q1>
+DEV_INLINE void tc_drain_range(uint32_t trow, int64_t (&W)[TcCfg<P>::G][TcCfg<P>::HALF]) {
+    using Cfg = TcCfg<P>;
+    constexpr int S = Cfg::S, NT = Cfg::NT, HALF = Cfg::HALF;
+    if constexpr (Q0 < Q1) {
+        constexpr int Q2 = (Q0 + 4 < Q1) ? Q0 + 4 : Q1;
+        float v[4][HALF];
+#pragma unroll
+        for (int r = 0; r < Q2 - Q0; ++r) tc_ld<HALF>(trow + (uint32_t)((Q0 + r) * NT), v[r]);
+        tc_wait_ld();
+#pragma unroll
+        for (int r = 0; r < Q2 - Q0; ++r) {
+            const int d = S - 1 - (Q0 + r);
+#pragma unroll
+            for (int j = 0; j < HALF; ++j)
+                W[d >> 2][j] += (int64_t)__float2int_rz(v[r][j]) * ((int64_t)1 << (8 * (d & 3)));
+        }
+        tc_drain_range<P, Q2, Q1>(trow, W);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -337,7 +403,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     auto emptyA = [&](uint32_t s) { return bar0 + 8u * (NA + s); };
     auto fullB = [&](uint32_t s) { return bar0 + 8u * (2 * NA + s); };
     auto emptyB = [&](uint32_t s) { return bar0 + 8u * (2 * NA + NB + s); };
-    const uint32_t tfull = bar0 + 8u * (2 * NA + 2 * NB), tempty = tfull + 8u, tfinal = tfull + 16u;
+    // TMEM hand-over per region (low diagonals q < Q, high q >= Q): full =
+    // the MMAs of a drain group are done, empty = the drain warps have read it
+    const uint32_t tfull_lo = bar0 + 8u * (2 * NA + 2 * NB), tfull_hi = tfull_lo + 8u, tempty_lo = tfull_lo + 16u,
+                   tempty_hi = tfull_lo + 24u, tfinal = tfull_lo + 32u;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t mtiles = (M + kTcRows - 1) / kTcRows;
@@ -357,11 +426,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(fullB(s), 1);
             mbar_init(emptyB(s), 1);
         }
-        mbar_init(tfull, 1);
-        mbar_init(tempty, 8);
+        mbar_init(tfull_lo, 1);
+        mbar_init(tfull_hi, 1);
+        mbar_init(tempty_lo, 8);
+        mbar_init(tempty_hi, 8);
         mbar_init(tfinal, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (Cfg::ZP > 0) {  // the zero slices in front of every B stack (never overwritten)
+        for (int st = 0; st < NB; ++st)
+            for (int o = threadIdx.x; o < Cfg::ZP * NT * 8; o += blockDim.x)
+                reinterpret_cast<uint32_t*>(sB + st * Cfg::BBYTES)[o] = 0u;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
         tmem_alloc(smem_addr(tslot), Cfg::TALLOC);
@@ -381,9 +458,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int64_t kb = kb0; kb < kb1 && ok; ++kb) {
                 const uint32_t sb = ib % NB;
                 if (!(ok = mbar_wait(emptyB(sb), ((ib / NB) & 1) ^ 1, lim, abort_flag))) break;
-                mbar_expect_tx(fullB(sb), Cfg::BBYTES);
-                bulk_copy_g2s(sB0 + sb * Cfg::BBYTES, Bs + ((nt * KB16 + kb) * SP) * (NT * 16), Cfg::BBYTES,
-                              fullB(sb));
+                mbar_expect_tx(fullB(sb), Cfg::BCOPY);
+                bulk_copy_g2s(sB0 + sb * Cfg::BBYTES + Cfg::ZP * NT * 32, Bs + ((nt * KB16 + kb) * SP) * (NT * 16),
+                              Cfg::BCOPY, fullB(sb));
                 ++ib;
                 for (int s0 = 0; s0 < S; s0 += Cfg::SB) {
                     const int ns = (S - s0 < Cfg::SB) ? S - s0 : Cfg::SB;
@@ -406,8 +483,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
     } else if (warp == 9) {
-        // ---- MMAs: one per A slice (two where N would pass 256); one wait
-        //      and one commit per stage of SB slices
+        // ---- MMAs: per k16 block a low pass and a high pass, one MMA per
+        //      slice and pass; one wait per stage, one commit per stage
         if (lane == 0) {
             uint32_t ia = 0, ib = 0, grp = 0;
             bool ok = kb1 > kb0;
@@ -415,8 +492,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int64_t rel = kb - kb0;
                 const bool gfirst = (rel % DK) == 0;
                 const bool glast = (rel % DK) == DK - 1 || kb == kb1 - 1;
+                const uint32_t acc0 = gfirst ? 0u : 1u;
                 if (gfirst && grp > 0) {
-                    if (!(ok = mbar_wait(tempty, (grp - 1) & 1, lim, abort_flag))) break;
+                    if (!(ok = mbar_wait(tempty_lo, (grp - 1) & 1, lim, abort_flag))) break;
                 }
                 const uint32_t sb = ib % NB;
                 if (!(ok = mbar_wait(fullB(sb), (ib / NB) & 1, lim, abort_flag))) break;
@@ -424,11 +502,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 // the start-address field is the descriptor's low bits: a
                 // byte offset o moves it by o >> 4
                 const uint64_t bd0 = tc_smem_desc(sB0 + sb * Cfg::BBYTES);
-                if (!(ok = tc_issue_k16<P, 0>(tbase, sA0, bd0, gfirst ? 0u : 1u, ia, bar0, lim, abort_flag))) break;
+                if (!(ok = tc_issue_low<P, 0>(tbase, sA0, bd0, acc0, ia, bar0, lim, abort_flag))) break;
+                if (glast) tc_commit(tfull_lo);
+                if (gfirst && grp > 0) {
+                    if (!(ok = mbar_wait(tempty_hi, (grp - 1) & 1, lim, abort_flag))) break;
+                    tc_fence_after();
+                }
+                if (!(ok = tc_issue_high<P, 0>(tbase, sA0, bd0, acc0, ia, bar0, lim, abort_flag))) break;
+                ia += Cfg::NBAT;
                 tc_commit(emptyB(sb));
                 ++ib;
                 if (glast) {
-                    tc_commit(tfull);
+                    tc_commit(tfull_hi);
                     ++grp;
                 }
             }
@@ -447,34 +532,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int j = 0; j < HALF; ++j) W[g][j] = 0;
         bool ok = true;
         for (int64_t gi = 0; gi < ngroups; ++gi) {
-            ok = mbar_wait(tfull, (uint32_t)(gi & 1), lim, abort_flag);
+            ok = mbar_wait(tfull_lo, (uint32_t)(gi & 1), lim, abort_flag);
             if (!__all_sync(0xffffffffu, ok)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                float v[4][HALF];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int q = S - 1 - 4 * g - r;
-                    if (q >= 0) tc_ld<HALF>(trow + (uint32_t)(q * NT), v[r]);
-                }
-                tc_wait_ld();
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int q = S - 1 - 4 * g - r;
-                    if (q >= 0) {
-#pragma unroll
-                        for (int j = 0; j < HALF; ++j)
-                            W[g][j] += (int64_t)__float2int_rz(v[r][j]) * ((int64_t)1 << (8 * r));
-                    }
-                }
-            }
+            tc_drain_range<P, 0, Cfg::Q>(trow, W);
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(tempty);
+            if (lane == 0) mbar_arrive(tempty_lo);
+            ok = mbar_wait(tfull_hi, (uint32_t)(gi & 1), lim, abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            tc_drain_range<P, Cfg::Q, S>(trow, W);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_hi);
         }
         if (ok) {
             // every MMA has completed and every copy has landed, so the A
