@@ -33,6 +33,14 @@ constexpr int fx_block_threads() {
         if (cudaGetLastError() != cudaSuccess) return MDLS_ERR_CUDA; \
     } while (0)
 
+// Width of the diagonal leaves of T (the WY form): each leaf is a serial
+// chain of L - 1 md steps on one warp, the levels above it parallel
+// products; the longer md operations of qd and od favour shorter chains.
+template <int P>
+constexpr int wy_leaf() {
+    return P == 2 ? 16 : 8;
+}
+
 // Per-device values looked up once (the current device's index selects the
 // slot; devices beyond kMaxDev share the last slot's lookup each time).
 constexpr int kMaxDev = 64;
@@ -521,7 +529,8 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
         int rc = launch_gemm<P>(ST_W, s, sbk, w, w, r, Yt, Y, Dense{G, t, tt2}, false, false, true);
         if (rc) return rc;
         {
-            const int L = w < kTriLeaf ? w : kTriLeaf;
+            constexpr int kLeaf = wy_leaf<P>();
+            const int L = w < kLeaf ? w : kLeaf;
             StageScope sc(ST_W, s);
             // one warp (two rows) per block: the leaves spread over w/2 SMs
             wy_t_leaf_kernel<P><<<(unsigned)((w + 1) / 2), 32, 0, s>>>(G, t, tt2, beta, t, w, L, T, t, tt2);
