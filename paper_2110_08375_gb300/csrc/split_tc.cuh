@@ -31,12 +31,12 @@
 // (tcgen05.ld), converted to integers and added into int64 words (four
 // diagonals per word, 2^8 apart), and the next k16 block overwrites them.
 //
-// Roles (320 threads, one block per SM): warp 8 lane 0 streams operands with
+// Roles (576 threads, one block per SM): warp 16 lane 0 streams operands with
 // cp.async.bulk into a ring of stages of SB A slice tiles (4 KB each; the low
 // pass's stages stay in until the high pass has read them again) and a ring
-// of B stacks, completing on mbarriers; warp 9 lane 0 issues tcgen05.mma and
-// tcgen05.commit; warps 0-7 read TMEM (warp w reads lanes 32 (w mod 4) ...,
-// half w / 4 of the NT columns), keep the exact words, and write the result
+// of B stacks, completing on mbarriers; warp 17 lane 0 issues tcgen05.mma and
+// tcgen05.commit; warps 0-15 read TMEM (warp w reads lanes 32 (w mod 4) ...,
+// quarter w / 4 of the NT columns), keep the exact words, and write the result
 // (to C, or as one md partial product when K is split over blocks).  Every
 // mbarrier wait is bounded by the workspace header's limit; a block that
 // gives up records MDLS_ERR_TIMEOUT, lets its copies and MMAs in flight
@@ -67,7 +67,7 @@ struct TcCfg {
     static constexpr int SP = P == 8 ? S + 1 : S;      // B slices per stack (od: one zero slice)
     static constexpr int DK = 1024 / (16 * S);         // k16 blocks per drain: 4, 2, 1
     static constexpr int G = (S + 3) / 4;              // int64 words per output
-    static constexpr int HALF = NT / 2;                // columns per drain thread
+    static constexpr int CPT = NT / 4;                 // columns per drain thread (4 warps per TMEM lane quarter)
     static constexpr int TCOLS = SP * NT;              // TMEM columns used: 240, 448, 448
     static constexpr int TALLOC = TCOLS <= 256 ? 256 : 512;
     static constexpr int SB = 8;                       // A slices per stage (one bulk copy)
@@ -85,11 +85,12 @@ struct TcCfg {
     static_assert(Q % SB == 0 && Q < S && QS < NA, "the low pass's stages stay resident beside one more");
     static_assert(Q * NT <= 256 && (S - Q + 1) * NT <= 256, "one MMA per slice and pass");
     static_assert(DK >= 1 && TCOLS <= 512, "digit diagonals must fit TMEM");
-    static_assert((size_t)HALF * G * 256 * 8 <= (size_t)NA * SB * 128 * 16 * 2, "the epilogue's words fit the A ring");
+    static_assert((size_t)CPT * G * 512 * 8 <= (size_t)NA * SB * 128 * 16 * 2, "the epilogue's words fit the A ring");
 };
 
 constexpr int kTcRows = 128;     // MMA M: one TMEM lane per output row
-constexpr int kTcThreads = 320;  // 8 drain warps, a copy warp, an MMA warp
+constexpr int kTcDrainWarps = 16;                    // 4 per TMEM lane quarter
+constexpr int kTcThreads = 32 * (kTcDrainWarps + 2);  // the drain warps, a copy warp, an MMA warp
 
 template <int P>
 constexpr size_t split_tc_smem() {
@@ -174,6 +175,13 @@ DEV_INLINE void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" :::
 
 template <int X>
 DEV_INLINE void tc_ld(uint32_t taddr, float (&v)[X]);
+template <>
+DEV_INLINE void tc_ld<2>(uint32_t taddr, float (&v)[2]) {
+    uint32_t r[2];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr) : "memory");
+    v[0] = __uint_as_float(r[0]);
+    v[1] = __uint_as_float(r[1]);
+}
 template <>
 DEV_INLINE void tc_ld<4>(uint32_t taddr, float (&v)[4]) {
     uint32_t r[4];
@@ -355,20 +363,20 @@ DEV_INLINE bool tc_issue_high(uint32_t tbase, uint32_t sA0, uint64_t bd0, uint32
 // tcgen05.ld per wait, each value (an integer below 2^24 in magnitude, exact
 // in fp32) added into its int64 word (D_q at bit 8 (S-1-q)).
 template <int P, int Q0, int Q1>
-DEV_INLINE void tc_drain_range(uint32_t trow, int64_t (&W)[TcCfg<P>::G][TcCfg<P>::HALF]) {
+DEV_INLINE void tc_drain_range(uint32_t trow, int64_t (&W)[TcCfg<P>::G][TcCfg<P>::CPT]) {
     using Cfg = TcCfg<P>;
-    constexpr int S = Cfg::S, NT = Cfg::NT, HALF = Cfg::HALF;
+    constexpr int S = Cfg::S, NT = Cfg::NT, CPT = Cfg::CPT;
     if constexpr (Q0 < Q1) {
         constexpr int Q2 = (Q0 + 4 < Q1) ? Q0 + 4 : Q1;
-        float v[4][HALF];
+        float v[4][CPT];
 #pragma unroll
-        for (int r = 0; r < Q2 - Q0; ++r) tc_ld<HALF>(trow + (uint32_t)((Q0 + r) * NT), v[r]);
+        for (int r = 0; r < Q2 - Q0; ++r) tc_ld<CPT>(trow + (uint32_t)((Q0 + r) * NT), v[r]);
         tc_wait_ld();
 #pragma unroll
         for (int r = 0; r < Q2 - Q0; ++r) {
             const int d = S - 1 - (Q0 + r);
 #pragma unroll
-            for (int j = 0; j < HALF; ++j)
+            for (int j = 0; j < CPT; ++j)
                 W[d >> 2][j] += (int64_t)__float2int_rz(v[r][j]) * ((int64_t)1 << (8 * (d & 3)));
         }
         tc_drain_range<P, Q2, Q1>(trow, W);
@@ -390,7 +398,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                          const int* __restrict__ fb, Dense C, int negate, int accumulate, int64_t part_stride,
                          WsHeader* hdr) {
     using Cfg = TcCfg<P>;
-    constexpr int S = Cfg::S, NT = Cfg::NT, SP = Cfg::SP, DK = Cfg::DK, G = Cfg::G, HALF = Cfg::HALF;
+    constexpr int S = Cfg::S, NT = Cfg::NT, SP = Cfg::SP, DK = Cfg::DK, G = Cfg::G, CPT = Cfg::CPT;
     constexpr int NA = Cfg::NA, NB = Cfg::NB;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char* sA = tc_smem;
@@ -428,8 +436,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         mbar_init(tfull_lo, 1);
         mbar_init(tfull_hi, 1);
-        mbar_init(tempty_lo, 8);
-        mbar_init(tempty_hi, 8);
+        mbar_init(tempty_lo, kTcDrainWarps);
+        mbar_init(tempty_hi, kTcDrainWarps);
         mbar_init(tfinal, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -449,7 +457,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(tslot);
 
-    if (warp == 8) {
+    if (warp == kTcDrainWarps) {
         // ---- copies: per k16 block the B stack, then the A slice tiles in
         //      stages of SB (contiguous in the tiled layout: one copy each)
         if (lane == 0 && kb1 > kb0) {
@@ -482,7 +490,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 mbar_wait(fullB(s), (last / NB) & 1, lim, abort_flag);
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == kTcDrainWarps + 1) {
         // ---- MMAs: per k16 block a low pass and a high pass, one MMA per
         //      slice and pass; one wait per stage, one commit per stage
         if (lane == 0) {
@@ -523,13 +531,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else {
         // ---- drain: exact words of this thread's row and columns
-        const int quarter = warp & 3, half = warp >> 2;
-        const uint32_t trow = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(half * HALF);
-        int64_t W[G][HALF];
+        const int quarter = warp & 3, part = warp >> 2;
+        const uint32_t trow = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(part * CPT);
+        int64_t W[G][CPT];
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
-            for (int j = 0; j < HALF; ++j) W[g][j] = 0;
+            for (int j = 0; j < CPT; ++j) W[g][j] = 0;
         bool ok = true;
         for (int64_t gi = 0; gi < ngroups; ++gi) {
             ok = mbar_wait(tfull_lo, (uint32_t)(gi & 1), lim, abort_flag);
@@ -559,25 +567,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // one rolled copy of the conversion serves the thread's columns
             // (unrolled per column, the conversion code outgrew the
             // instruction cache)
-            int64_t* sW = reinterpret_cast<int64_t*>(sA) + (threadIdx.x & 255);
+            int64_t* sW = reinterpret_cast<int64_t*>(sA) + threadIdx.x;
 #pragma unroll
-            for (int j = 0; j < HALF; ++j)
+            for (int j = 0; j < CPT; ++j)
 #pragma unroll
-                for (int g = 0; g < G; ++g) sW[(j * G + g) * 256] = negate ? -W[g][j] : W[g][j];
+                for (int g = 0; g < G; ++g) sW[(j * G + g) * 512] = negate ? -W[g][j] : W[g][j];
             const int64_t i = mt * kTcRows + 32 * quarter + lane;
             if (i < M) {
                 const int sci = ea[i];
                 double* base = C.ptr + (int64_t)blockIdx.y * part_stride;
 #pragma unroll 1
-                for (int j = 0; j < HALF; ++j) {
-                    const int64_t jc = nt * NT + half * HALF + j;
+                for (int j = 0; j < CPT; ++j) {
+                    const int64_t jc = nt * NT + part * CPT + j;
                     if (jc >= N) break;
                     // value = 2^e0 sum_g W_g 2^(32 g) exactly (D_q at bit
                     // 8 (S-1-q)); C's old value joins it on the integer pipe
                     const int e0 = sci + fb[jc] - 8 * (S + 1);
                     int64_t w[G + 3];
 #pragma unroll
-                    for (int g = 0; g < G; ++g) w[g] = sW[(j * G + g) * 256];
+                    for (int g = 0; g < G; ++g) w[g] = sW[(j * G + g) * 512];
 #pragma unroll
                     for (int g = G; g < G + 3; ++g) w[g] = 0;
                     st_md<P>(base, C.ps, jc * C.ld + i,
