@@ -293,9 +293,9 @@ int launch_gemv(int stage, cudaStream_t st, SplitBuf sb, int64_t M, int64_t K, A
 template <int P>
 int tri_levels(int stage, cudaStream_t st, double* X, int64_t ldx, int64_t psx, int64_t xtile,
                const double* M, int64_t ldm, int64_t psm, int64_t mtile, int64_t n, int t,
-               int64_t ntiles, int L) {
+               int64_t ntiles, int L, int s_end = 1 << 30) {
     StageScope sc(stage, st);
-    for (int s = L; s < t; s *= 2) {
+    for (int s = L; s < t && s < s_end; s *= 2) {
         const int nbi = (s + 7) / 8, nbj = (s + 3) / 4;
         // k groups of at least 8 values of k (16 for s = 128) when the level
         // has few blocks; of at least 32 when the blocks of all tiles already
@@ -535,8 +535,32 @@ int qr_run(int64_t m, int64_t n, int nextra, double* A, int64_t lda, int64_t psa
             // one warp (two rows) per block: the leaves spread over w/2 SMs
             wy_t_leaf_kernel<P><<<(unsigned)((w + 1) / 2), 32, 0, s>>>(G, t, tt2, beta, t, w, L, T, t, tt2);
             MDLS_LAUNCH_CHECK();
-            rc = tri_levels<P>(ST_W, s, T, t, tt2, 0, G, t, tt2, 0, w, w, 1, L);
+            // in octo double split mode the levels of 32 columns and more are
+            // split products (tensor cores); the narrower ones, and every level
+            // in dd and qd (measured: their shorter md operations make the FP64
+            // levels cheaper than the products' launches), stay on the FP64 pipe
+            constexpr int kSplitLevel = 32;
+            const bool split_levels = P == 8 && sbk.tc != nullptr;
+            rc = tri_levels<P>(ST_W, s, T, t, tt2, 0, G, t, tt2, 0, w, w, 1, L, split_levels ? kSplitLevel : 1 << 30);
             if (rc) return rc;
+            if (split_levels) {
+                for (int lv = kSplitLevel > L ? kSplitLevel : L; lv < w; lv *= 2)
+                    for (int a = 0; a + lv < w; a += 2 * lv) {
+                        const int s2 = (w - a - lv) < lv ? (w - a - lv) : lv;
+                        // T12 = -T1 (G12 T2): Z^T = T2^T G12^T into the unused
+                        // lower block (rows a+lv.., columns a..), then T12 = -T1 Z
+                        double* Tl = T + (int64_t)a * t + a + lv;
+                        rc = launch_gemm<P>(ST_W, s, sbk, s2, lv, s2,
+                                            ViewUpperT{T + (int64_t)(a + lv) * t + a + lv, t, tt2},
+                                            ViewDenseT{G + (int64_t)(a + lv) * t + a, t, tt2}, Dense{Tl, t, tt2},
+                                            false, false);
+                        if (rc) return rc;
+                        rc = launch_gemm<P>(ST_W, s, sbk, lv, s2, lv, ViewUpper{T + (int64_t)a * t + a, t, tt2},
+                                            ViewDenseT{Tl, t, tt2}, Dense{T + (int64_t)(a + lv) * t + a, t, tt2},
+                                            true, false);
+                        if (rc) return rc;
+                    }
+            }
         }
         return launch_gemm<P>(ST_W, s, sbk, r, w, w, Y, ViewUpper{T, t, tt2}, Dense{wy_w(k), ldw, psw}, true,
                               false);
